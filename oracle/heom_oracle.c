@@ -1,0 +1,497 @@
+/*
+ * heom_oracle.c -- plain, slow, FP64 CPU statement of the HEOM right-hand side and its classic
+ * RK4 integration, written from the paper (Kramer, Noack, Reinefeld, Rodriguez, Zhang,
+ * "Efficient calculation of open quantum system dynamics and time-resolved spectroscopy with
+ * Distributed Memory HEOM (DM-HEOM)", arXiv 1803.03498).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the cpu_baseline / reference
+ * arm of bench.py load this library.  It shares no code, header, table or constant with the CUDA
+ * library in paper_1803_03498_gb300/; the two are independent statements of the same method.
+ *
+ * What each part follows:
+ *   - hierarchy (tuples, numbering, +/- links): section "HEOM formalism", Eq. (Nmatrices) and the
+ *     paragraph on "+" and "-" vertices; mode index l = (b-1)K + k + 1 (0-based here: l = b*K + k).
+ *     The paper leaves the order of the consecutive numbering u open; this oracle orders tuples by
+ *     level |n| and, inside a level, by colexicographic order of the stars-and-bars bar positions
+ *     (a sort with an explicit comparator, not a ranking formula).
+ *   - bath coefficients gamma(b,k), c(b,k) and the terminator: Eq. (HEOM) and its definitions
+ *     (Matsubara expansion of a Drude-Lorentz density, Omega = 0).
+ *   - right-hand side: Eq. (HEOM) term by term, with the superoperators V^x, V^x V^x and V^o
+ *     written with the Kronecker deltas of their element-wise definitions, and the ADO rescaling
+ *     (section "HEOM formalism", last two substitutions).
+ *   - integrator: classic four-stage Runge-Kutta with four ADO copies (section "HEOM memory and
+ *     compute requirements" and "Distributed memory HEOM implementation").
+ *   - observables: rho = sigma_0; site populations; trace; the linear-absorption dipole
+ *     correlation sum_a w_a sigma_0[a][0] (Eq. lin_abs_mukamel with mu^+ |0><0| as start).
+ *
+ * Units: energies in cm^-1 are turned into angular frequencies in rad/fs by 2*pi*c with
+ * c = 2.99792458e-5 cm/fs; hbar = 1 in these units; times in fs; beta = 1/(k_B T) with
+ * k_B = 0.6950348004 cm^-1/K (exact from the 2019 SI constants).  The paper is silent on units.
+ *
+ * Readings of the paper (each also listed in the project's design notes):
+ *   - one bath per coupled state (S(b) = 1): V_b = |s_b><s_b|; several baths may share a state.
+ *   - K here is the number of Matsubara terms beyond the Drude term, so each bath has K+1 modes.
+ *   - hbar = 1 throughout (the paper's hbar placement is not consistent).
+ *   - the rescaling uses |c(b,k)| of the real c of the paper; when |c| < 1e-300 the mode is left
+ *     unscaled (up factor 1, down factor n).
+ *   - Parity with printed trajectories is unpinned: the paper prints none.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TWO_PI_C 1.8836515673088532e-4 /* rad/fs per cm^-1 */
+#define ORC_KB_CM 0.6950348004             /* cm^-1 per K */
+#define ORC_PI 3.14159265358979323846
+
+typedef double complex cplx;
+
+typedef struct {
+  int M, D;
+  int64_t n;          /* number of tuples */
+  uint8_t *tuples;    /* [n][M] */
+  int32_t *plus;      /* [n][M], -1 if invalid */
+  int32_t *minus;     /* [n][M], -1 if invalid */
+} orc_hier;
+
+typedef struct {
+  int N;              /* n_states */
+  cplx *H;            /* [N][N] rad/fs */
+  int B, K;           /* baths, Matsubara terms beyond Drude (modes per bath = K+1) */
+  int *bath_state;    /* [B] */
+  double *lambda, *nu, *beta; /* [B] rad/fs, 1/fs, fs */
+  int terminator, rescale;
+  /* per mode l = b*(K+1) + k */
+  int M;
+  double *gamma, *c, *lamnu; /* lamnu = lambda*nu for k = 0, else 0 */
+  double *delta_b;           /* [B] terminator coefficient */
+  orc_hier h;
+} orc_model;
+
+/* ------------------------------------------------------------------------------------------ */
+/* Hierarchy: all n in N^M with |n| <= D (Eq. Nmatrices), sorted by (level, colex of bars).    */
+
+static int g_cmp_M; /* comparator context (single-threaded oracle) */
+
+static void bars_of(const uint8_t *n, int M, int *b) {
+  /* bar j (j = 1..M-1) sits after the stars of modes 1..j: b_j = (j-1) + sum_{i<=j} n_i */
+  int s = 0;
+  for (int j = 1; j <= M - 1; ++j) {
+    s += n[j - 1];
+    b[j - 1] = (j - 1) + s;
+  }
+}
+
+static int level_of(const uint8_t *n, int M) {
+  int s = 0;
+  for (int i = 0; i < M; ++i) s += n[i];
+  return s;
+}
+
+static int tuple_cmp(const void *pa, const void *pb) {
+  const uint8_t *a = (const uint8_t *)pa, *b = (const uint8_t *)pb;
+  int M = g_cmp_M;
+  int la = level_of(a, M), lb = level_of(b, M);
+  if (la != lb) return la < lb ? -1 : 1;
+  if (M <= 1) return 0;
+  int ba[256], bb[256];
+  bars_of(a, M, ba);
+  bars_of(b, M, bb);
+  /* colex: the set whose largest differing element is smaller comes first */
+  for (int j = M - 2; j >= 0; --j)
+    if (ba[j] != bb[j]) return ba[j] < bb[j] ? -1 : 1;
+  return 0;
+}
+
+static void enum_rec(int M, int D, int pos, int left, uint8_t *cur, uint8_t *out, int64_t *cnt) {
+  if (pos == M) {
+    memcpy(out + (*cnt) * M, cur, (size_t)M);
+    ++*cnt;
+    return;
+  }
+  for (int v = 0; v <= left; ++v) {
+    cur[pos] = (uint8_t)v;
+    enum_rec(M, D, pos + 1, left - v, cur, out, cnt);
+  }
+  cur[pos] = 0;
+}
+
+static int64_t count_rec(int M, int pos, int left) {
+  if (pos == M) return 1;
+  int64_t s = 0;
+  for (int v = 0; v <= left; ++v) s += count_rec(M, pos + 1, left - v);
+  return s;
+}
+
+/* Lookup of a tuple's position: open-addressing hash table over the tuple bytes (FNV-1a). */
+typedef struct {
+  int64_t cap;
+  int64_t *slot; /* position in the sorted tuple list, -1 = empty */
+} orc_index;
+
+static uint64_t fnv1a(const uint8_t *k, int M) {
+  uint64_t h = 1469598103934665603ULL;
+  for (int i = 0; i < M; ++i) { h ^= k[i]; h *= 1099511628211ULL; }
+  return h;
+}
+
+static int index_build(orc_index *ix, const orc_hier *h) {
+  ix->cap = 1;
+  while (ix->cap < 2 * h->n + 1) ix->cap <<= 1;
+  ix->slot = (int64_t *)malloc(sizeof(int64_t) * ix->cap);
+  if (!ix->slot) return -3;
+  for (int64_t i = 0; i < ix->cap; ++i) ix->slot[i] = -1;
+  for (int64_t u = 0; u < h->n; ++u) {
+    uint64_t p = fnv1a(h->tuples + u * h->M, h->M) & (uint64_t)(ix->cap - 1);
+    while (ix->slot[p] >= 0) p = (p + 1) & (uint64_t)(ix->cap - 1);
+    ix->slot[p] = u;
+  }
+  return 0;
+}
+
+static int64_t find_tuple(const orc_hier *h, const orc_index *ix, const uint8_t *key) {
+  uint64_t p = fnv1a(key, h->M) & (uint64_t)(ix->cap - 1);
+  while (ix->slot[p] >= 0) {
+    if (memcmp(h->tuples + ix->slot[p] * h->M, key, (size_t)h->M) == 0) return ix->slot[p];
+    p = (p + 1) & (uint64_t)(ix->cap - 1);
+  }
+  return -1;
+}
+
+static int hier_build(orc_hier *h, int M, int D) {
+  if (M < 1 || M > 256 || D < 0 || D > 255) return -1;
+  h->M = M;
+  h->D = D;
+  h->n = count_rec(M, 0, D); /* brute-force count, pinned against C(M+D, D) in the tests */
+  if (h->n > INT32_MAX) return -2;
+  h->tuples = (uint8_t *)calloc((size_t)h->n * M, 1);
+  h->plus = (int32_t *)malloc((size_t)h->n * M * sizeof(int32_t));
+  h->minus = (int32_t *)malloc((size_t)h->n * M * sizeof(int32_t));
+  if (!h->tuples || !h->plus || !h->minus) return -3;
+  uint8_t cur[256] = {0};
+  int64_t cnt = 0;
+  enum_rec(M, D, 0, D, cur, h->tuples, &cnt);
+  g_cmp_M = M;
+  qsort(h->tuples, (size_t)h->n, (size_t)M, tuple_cmp);
+  orc_index ix;
+  if (index_build(&ix, h)) return -3;
+  /* "+" link: n + e_l valid iff |n| + 1 <= D.  "-" link: n - e_l valid iff n_l >= 1. */
+  uint8_t key[256];
+  for (int64_t u = 0; u < h->n; ++u) {
+    const uint8_t *nu = h->tuples + u * M;
+    int L = level_of(nu, M);
+    for (int l = 0; l < M; ++l) {
+      memcpy(key, nu, (size_t)M);
+      if (L + 1 <= D) {
+        key[l] = (uint8_t)(nu[l] + 1);
+        h->plus[u * M + l] = (int32_t)find_tuple(h, &ix, key);
+      } else {
+        h->plus[u * M + l] = -1;
+      }
+      memcpy(key, nu, (size_t)M);
+      if (nu[l] >= 1) {
+        key[l] = (uint8_t)(nu[l] - 1);
+        h->minus[u * M + l] = (int32_t)find_tuple(h, &ix, key);
+      } else {
+        h->minus[u * M + l] = -1;
+      }
+    }
+  }
+  free(ix.slot);
+  return 0;
+}
+
+static void hier_free(orc_hier *h) {
+  free(h->tuples);
+  free(h->plus);
+  free(h->minus);
+  memset(h, 0, sizeof(*h));
+}
+
+int64_t orc_hier_count(int M, int D) {
+  if (M < 1 || D < 0) return -1;
+  return count_rec(M, 0, D);
+}
+
+/* Build the hierarchy and copy it out: tuples [n][M] uint8, plus/minus [n][M] int32. */
+int orc_hier_export(int M, int D, int64_t cap, uint8_t *tuples, int32_t *plus, int32_t *minus) {
+  orc_hier h;
+  memset(&h, 0, sizeof(h));
+  int rc = hier_build(&h, M, D);
+  if (rc) { hier_free(&h); return rc; }
+  if (h.n > cap) { hier_free(&h); return -4; }
+  memcpy(tuples, h.tuples, (size_t)h.n * M);
+  memcpy(plus, h.plus, (size_t)h.n * M * sizeof(int32_t));
+  memcpy(minus, h.minus, (size_t)h.n * M * sizeof(int32_t));
+  hier_free(&h);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Model set-up: units and the Matsubara coefficients of Eq. (HEOM).                           */
+
+void orc_destroy(orc_model *m) {
+  if (!m) return;
+  free(m->H);
+  free(m->bath_state);
+  free(m->lambda);
+  free(m->nu);
+  free(m->beta);
+  free(m->gamma);
+  free(m->c);
+  free(m->lamnu);
+  free(m->delta_b);
+  hier_free(&m->h);
+  free(m);
+}
+
+/* H_re/H_im: [N][N] row-major in cm^-1 (H_im may be NULL).  Returns NULL on bad input. */
+orc_model *orc_create(int N, const double *H_re, const double *H_im, int B, const int *bath_state,
+                      const double *lambda_cm, const double *tau_fs, const double *T_K, int K,
+                      int D, int terminator, int rescale) {
+  if (N < 1 || B < 1 || K < 0 || D < 0) return NULL;
+  orc_model *m = (orc_model *)calloc(1, sizeof(orc_model));
+  m->N = N;
+  m->B = B;
+  m->K = K;
+  m->terminator = terminator;
+  m->rescale = rescale;
+  m->H = (cplx *)malloc(sizeof(cplx) * N * N);
+  for (int i = 0; i < N * N; ++i)
+    m->H[i] = ORC_TWO_PI_C * (H_re[i] + I * (H_im ? H_im[i] : 0.0));
+  m->bath_state = (int *)malloc(sizeof(int) * B);
+  m->lambda = (double *)malloc(sizeof(double) * B);
+  m->nu = (double *)malloc(sizeof(double) * B);
+  m->beta = (double *)malloc(sizeof(double) * B);
+  m->delta_b = (double *)malloc(sizeof(double) * B);
+  m->M = B * (K + 1);
+  m->gamma = (double *)malloc(sizeof(double) * m->M);
+  m->c = (double *)malloc(sizeof(double) * m->M);
+  m->lamnu = (double *)malloc(sizeof(double) * m->M);
+  for (int b = 0; b < B; ++b) {
+    if (bath_state[b] < 0 || bath_state[b] >= N) { orc_destroy(m); return NULL; }
+    m->bath_state[b] = bath_state[b];
+    m->lambda[b] = ORC_TWO_PI_C * lambda_cm[b];
+    m->nu[b] = 1.0 / tau_fs[b];
+    m->beta[b] = 1.0 / (ORC_TWO_PI_C * ORC_KB_CM * T_K[b]);
+    double lam = m->lambda[b], nu = m->nu[b], beta = m->beta[b];
+    double sum_c_over_gamma = 0.0;
+    for (int k = 0; k <= K; ++k) {
+      int l = b * (K + 1) + k;
+      double g, c;
+      if (k == 0) {
+        g = nu;                                      /* gamma(b,0) = nu_b */
+        c = nu * lam / tan(beta * nu / 2.0);         /* c(b,0) = nu lambda cot(beta nu / 2) */
+      } else {
+        g = 2.0 * ORC_PI * k / beta;                   /* gamma(b,k) = 2 pi k / beta */
+        if (fabs(g * g - nu * nu) < 1e-6 * g * g) { orc_destroy(m); return NULL; } /* gamma_k = nu */
+        c = 4.0 * lam * nu / beta * g / (g * g - nu * nu);
+      }
+      m->gamma[l] = g;
+      m->c[l] = c;
+      m->lamnu[l] = (k == 0) ? lam * nu : 0.0;
+      sum_c_over_gamma += c / g;
+    }
+    /* terminator: 2 lambda / (beta nu) - sum_k c(b,k) / gamma(b,k) */
+    m->delta_b[b] = 2.0 * lam / (beta * nu) - sum_c_over_gamma;
+  }
+  memset(&m->h, 0, sizeof(m->h));
+  if (hier_build(&m->h, m->M, D)) { orc_destroy(m); return NULL; }
+  return m;
+}
+
+int64_t orc_n_ado(const orc_model *m) { return m->h.n; }
+int orc_n_modes(const orc_model *m) { return m->M; }
+
+/* gamma, c, lamnu: [M]; mode_state: [M]; delta_b: [B] */
+void orc_export_modes(const orc_model *m, double *gamma, double *c, double *lamnu, int *mode_state,
+                      double *delta_b) {
+  for (int l = 0; l < m->M; ++l) {
+    gamma[l] = m->gamma[l];
+    c[l] = m->c[l];
+    lamnu[l] = m->lamnu[l];
+    mode_state[l] = m->bath_state[l / (m->K + 1)];
+  }
+  for (int b = 0; b < m->B; ++b) delta_b[b] = m->delta_b[b];
+}
+
+void orc_export_hierarchy(const orc_model *m, uint8_t *tuples, int32_t *plus, int32_t *minus) {
+  memcpy(tuples, m->h.tuples, (size_t)m->h.n * m->M);
+  memcpy(plus, m->h.plus, (size_t)m->h.n * m->M * sizeof(int32_t));
+  memcpy(minus, m->h.minus, (size_t)m->h.n * m->M * sizeof(int32_t));
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Superoperators, element-wise from their delta definitions.                                  */
+
+static inline double kd(int a, int b) { return a == b ? 1.0 : 0.0; }
+/* (V_s^x A)_ij = (delta_is - delta_sj) A_ij */
+static inline double vx(int s, int i, int j) { return kd(i, s) - kd(s, j); }
+/* (V_s^x V_s^x A)_ij = (1 - delta_ij)(delta_is + delta_sj) A_ij */
+static inline double vxvx(int s, int i, int j) { return (1.0 - kd(i, j)) * (kd(i, s) + kd(s, j)); }
+/* (V_s^o A)_ij = (delta_is + delta_sj) A_ij */
+static inline double vo(int s, int i, int j) { return kd(i, s) + kd(s, j); }
+
+/* scale factors of the ADO rescaling */
+static double up_factor(const orc_model *m, int l, int n_l) {
+  double ac = fabs(m->c[l]);
+  if (!m->rescale || ac < 1e-300) return 1.0;
+  return sqrt((n_l + 1) * ac);
+}
+static double down_factor(const orc_model *m, int l, int n_l) {
+  double ac = fabs(m->c[l]);
+  if (!m->rescale || ac < 1e-300) return (double)n_l;
+  return sqrt(n_l / ac);
+}
+
+/* d sigma_u / dt for one ADO u.  in/out: [n][N][N] complex in split re/im arrays. */
+static void rhs_one(const orc_model *m, int64_t u, const double *in_re, const double *in_im,
+                    cplx *out /* [N][N] */) {
+  const int N = m->N, M = m->M, K1 = m->K + 1;
+  const int64_t NN = (int64_t)N * N;
+  const uint8_t *n = m->h.tuples + u * M;
+#define SIG(v, i, j) (in_re[(v) * NN + (i) * N + (j)] + I * in_im[(v) * NN + (i) * N + (j)])
+  /* -i [H, sigma_u] */
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      cplx acc = 0.0;
+      for (int k = 0; k < N; ++k) acc += m->H[i * N + k] * SIG(u, k, j) - SIG(u, i, k) * m->H[k * N + j];
+      out[i * N + j] = -I * acc;
+    }
+  /* - sigma_u sum_{b,k} n_{u,(b,k)} gamma(b,k) */
+  double gsum = 0.0;
+  for (int l = 0; l < M; ++l) gsum += n[l] * m->gamma[l];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) out[i * N + j] -= gsum * SIG(u, i, j);
+  /* - sum_b [2 lambda/(beta nu) - sum_k c/gamma] V^x V^x sigma_u */
+  if (m->terminator)
+    for (int b = 0; b < m->B; ++b) {
+      int s = m->bath_state[b];
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) out[i * N + j] -= m->delta_b[b] * vxvx(s, i, j) * SIG(u, i, j);
+    }
+  /* + sum i V^x sigma^+  and  + sum n theta sigma^-, with the rescaled factors */
+  for (int l = 0; l < M; ++l) {
+    int b = l / K1, k = l % K1, s = m->bath_state[b];
+    int32_t vp = m->h.plus[u * M + l], vm = m->h.minus[u * M + l];
+    if (vp >= 0) {
+      double f = up_factor(m, l, n[l]);
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) out[i * N + j] += I * f * vx(s, i, j) * SIG(vp, i, j);
+    }
+    if (vm >= 0) {
+      double f = down_factor(m, l, n[l]);
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+          /* theta = i c V^x + delta_{k0} lambda nu V^o */
+          cplx theta = I * m->c[l] * vx(s, i, j) + (k == 0 ? m->lamnu[l] : 0.0) * vo(s, i, j);
+          out[i * N + j] += f * theta * SIG(vm, i, j);
+        }
+    }
+  }
+#undef SIG
+}
+
+/* Full RHS over every ADO.  Arrays [n][N][N]. */
+void orc_rhs(const orc_model *m, const double *in_re, const double *in_im, double *out_re,
+             double *out_im) {
+  const int64_t NN = (int64_t)m->N * m->N;
+  cplx *tmp = (cplx *)malloc(sizeof(cplx) * NN);
+  for (int64_t u = 0; u < m->h.n; ++u) {
+    rhs_one(m, u, in_re, in_im, tmp);
+    for (int64_t e = 0; e < NN; ++e) {
+      out_re[u * NN + e] = creal(tmp[e]);
+      out_im[u * NN + e] = cimag(tmp[e]);
+    }
+  }
+  free(tmp);
+}
+
+/* RHS of a list of ADOs (sampled checks on large hierarchies).  out: [count][N][N]. */
+void orc_rhs_list(const orc_model *m, const int64_t *us, int64_t count, const double *in_re,
+                  const double *in_im, double *out_re, double *out_im) {
+  const int64_t NN = (int64_t)m->N * m->N;
+  cplx *tmp = (cplx *)malloc(sizeof(cplx) * NN);
+  for (int64_t t = 0; t < count; ++t) {
+    rhs_one(m, us[t], in_re, in_im, tmp);
+    for (int64_t e = 0; e < NN; ++e) {
+      out_re[t * NN + e] = creal(tmp[e]);
+      out_im[t * NN + e] = cimag(tmp[e]);
+    }
+  }
+  free(tmp);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Observables of rho = sigma_0.  One record: pop[N], tr_re, tr_im, corr_re, corr_im.          */
+
+int orc_record_len(const orc_model *m) { return m->N + 4; }
+
+static void record(const orc_model *m, const double *y_re, const double *y_im, const double *w,
+                   double *rec) {
+  const int N = m->N;
+  double tr_re = 0, tr_im = 0, cr = 0, ci = 0;
+  for (int a = 0; a < N; ++a) {
+    rec[a] = y_re[a * N + a];
+    tr_re += y_re[a * N + a];
+    tr_im += y_im[a * N + a];
+    if (w) {
+      cr += w[a] * y_re[a * N + 0];
+      ci += w[a] * y_im[a * N + 0];
+    }
+  }
+  rec[N] = tr_re;
+  rec[N + 1] = tr_im;
+  rec[N + 2] = cr;
+  rec[N + 3] = ci;
+}
+
+/* Classic RK4 with four ADO copies: k1 = f(y), k2 = f(y + h/2 k1), k3 = f(y + h/2 k2),
+ * k4 = f(y + h k3), y <- y + h/6 (k1 + 2 k2 + 2 k3 + k4).
+ * y: [n][N][N] split re/im, updated in place.  Records every obs_stride steps (after the step),
+ * plus one record of the start state; obs must hold (n_steps/obs_stride + 1) records.
+ * w: [N] weights of the dipole correlation (may be NULL). */
+int orc_rk4(const orc_model *m, double *y_re, double *y_im, double dt_fs, int64_t n_steps,
+            int64_t obs_stride, const double *w, double *obs) {
+  const int64_t tot = m->h.n * (int64_t)m->N * m->N;
+  double *k_re = (double *)malloc(sizeof(double) * tot), *k_im = (double *)malloc(sizeof(double) * tot);
+  double *x_re = (double *)malloc(sizeof(double) * tot), *x_im = (double *)malloc(sizeof(double) * tot);
+  double *a_re = (double *)malloc(sizeof(double) * tot), *a_im = (double *)malloc(sizeof(double) * tot);
+  if (!k_re || !k_im || !x_re || !x_im || !a_re || !a_im) {
+    free(k_re); free(k_im); free(x_re); free(x_im); free(a_re); free(a_im);
+    return -3;
+  }
+  const double h = dt_fs;
+  const double wacc[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const double anext[3] = {0.5, 0.5, 1.0};
+  int64_t rec_i = 0;
+  const int rl = orc_record_len(m);
+  if (obs) record(m, y_re, y_im, w, obs + (rec_i++) * rl);
+  for (int64_t step = 0; step < n_steps; ++step) {
+    memcpy(a_re, y_re, sizeof(double) * tot);
+    memcpy(a_im, y_im, sizeof(double) * tot);
+    const double *xin_re = y_re, *xin_im = y_im;
+    for (int s = 0; s < 4; ++s) {
+      orc_rhs(m, xin_re, xin_im, k_re, k_im);
+      for (int64_t e = 0; e < tot; ++e) {
+        a_re[e] += wacc[s] * h * k_re[e];
+        a_im[e] += wacc[s] * h * k_im[e];
+      }
+      if (s < 3) {
+        for (int64_t e = 0; e < tot; ++e) {
+          x_re[e] = y_re[e] + anext[s] * h * k_re[e];
+          x_im[e] = y_im[e] + anext[s] * h * k_im[e];
+        }
+        xin_re = x_re;
+        xin_im = x_im;
+      }
+    }
+    memcpy(y_re, a_re, sizeof(double) * tot);
+    memcpy(y_im, a_im, sizeof(double) * tot);
+    if (obs && obs_stride > 0 && (step + 1) % obs_stride == 0) record(m, y_re, y_im, w, obs + (rec_i++) * rl);
+  }
+  free(k_re); free(k_im); free(x_re); free(x_im); free(a_re); free(a_im);
+  return 0;
+}
