@@ -1,0 +1,174 @@
+/*
+ * heom.h -- C ABI of libheom, a single-GPU (GB300, sm_103a) propagator for the hierarchical
+ * equations of motion (HEOM) of a Frenkel-exciton system coupled to Drude-Lorentz baths, after
+ * arXiv 1803.03498 (DM-HEOM).
+ *
+ * Conventions for every call:
+ *   - Returns an int status: HEOM_OK (0) or a negative HEOM_E_* code.  heom_last_error() returns
+ *     a thread-local, human-readable message for the last failing call of the calling thread.
+ *     No C++ exception crosses this boundary.
+ *   - Energies in cm^-1, times in fs, temperatures in K.  Internally hbar = 1 with energies in
+ *     rad/fs (E[rad/fs] = 2 pi c E[cm^-1], c = 2.99792458e-5 cm/fs).
+ *   - Host matrices are row-major.  A hierarchy state on the host is ADO-major: [n_ado][N][N],
+ *     real and imaginary parts in two separate double arrays.
+ *   - The caller owns all device memory the run uses (one workspace block) and the CUDA stream;
+ *     the library owns only the small opaque handles.  Calls that launch work enqueue it on the
+ *     run's stream and return without waiting, except where stated ("synchronises").
+ *   - Asynchronous CUDA errors surface as HEOM_E_CUDA at the next synchronising call.
+ */
+#ifndef HEOM_H
+#define HEOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HEOM_OK 0
+#define HEOM_E_ARG (-1)      /* bad shape or parameter, Matsubara resonance, unstable time step */
+#define HEOM_E_OVERFLOW (-2) /* hierarchy size or an offset overflows int32 / int64 */
+#define HEOM_E_NOMEM (-3)    /* workspace too small, record buffer full, host allocation failed */
+#define HEOM_E_CUDA (-4)     /* a CUDA runtime call failed */
+#define HEOM_E_TIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define HEOM_E_NUMERIC (-6)  /* NaN/Inf detected in the root ADO */
+#define HEOM_E_STATE (-7)    /* call not valid for the handle's current state */
+
+/* Arithmetic of a run. */
+#define HEOM_FP64 0       /* every ADO stored and computed in FP64 */
+#define HEOM_FP32_MIXED 1 /* levels >= 2 stored and computed in FP32; levels 0 and 1 (the root ADO
+                             sigma_0 and its direct neighbours), the RK4 combination of sigma_0 and
+                             every observable reduction in FP64 */
+
+typedef struct heom_hier heom_hier;
+typedef struct heom_run heom_run;
+
+/*
+ * The physical model: H (n_states x n_states, Hermitian, cm^-1) and n_baths Drude-Lorentz baths
+ * (Omega = 0), bath b coupled to state bath_state[b] through V_b = |s><s| (Eq. HEOM, with S(b) = 1;
+ * several baths may couple to the same state, states without a bath get no bath terms).  Each
+ * bath contributes n_matsubara + 1 modes (the Drude term k = 0 and Matsubara terms k = 1..K), so
+ * the hierarchy has n_modes = n_baths * (n_matsubara + 1); mode l = b * (n_matsubara + 1) + k
+ * (the 0-based form of the paper's l = (b-1)K + k + 1).
+ * terminator: 1 adds the Matsubara terminator term of Eq. HEOM, 0 drops it.
+ * rescale: 1 applies the ADO rescaling (sqrt((n+1)|c|) up, sqrt(n/|c|) down), 0 uses 1 and n.
+ * All pointers are read during the call only (copied).
+ */
+typedef struct {
+  int n_states;
+  const double *H_re;      /* [n_states * n_states] */
+  const double *H_im;      /* [n_states * n_states] or NULL for a real H */
+  int n_baths;
+  const int *bath_state;   /* [n_baths], each in [0, n_states) */
+  const double *lambda_cm; /* [n_baths] reorganisation energy */
+  const double *tau_fs;    /* [n_baths] correlation time 1/nu */
+  const double *T_K;       /* [n_baths] temperature */
+  int n_matsubara;         /* K >= 0 */
+  int terminator;
+  int rescale;
+} heom_system;
+
+/* Message of the calling thread's last failing call ("" if none).  Valid until that thread's next
+ * call into the library. */
+const char *heom_last_error(void);
+
+/*
+ * heom_build_hierarchy -- enumerate every multi-index n in N^n_modes with |n| <= depth (Eq.
+ * Nmatrices: C(n_modes + depth, depth) ADOs) and build the "+"/"-" link tables (u -> n +- e_l,
+ * section "HEOM formalism").  Numbering u: by level |n|, then by the colexicographic rank of the
+ * stars-and-bars positions b_j = (j - 1) + n_1 + ... + n_j (j = 1..n_modes-1):
+ *     u = C(n_modes + L - 1, n_modes) [L > 0] + sum_j C(b_j, j).
+ * The root (all zeros) is u = 0.  Host-only; the tables are uploaded into a run's workspace at
+ * heom_run_create.  Errors: HEOM_E_ARG (n_modes < 1, n_modes > 255, depth < 0, depth > 255),
+ * HEOM_E_OVERFLOW (more than 2^31 - 1 ADOs), HEOM_E_NOMEM.  *out is owned by the caller and
+ * freed with heom_hier_destroy.
+ */
+int heom_build_hierarchy(int n_modes, int depth, heom_hier **out);
+int heom_hier_destroy(heom_hier *h);
+
+/* n_ado and, if level_offsets is not NULL, the first u of every level L = 0..depth plus n_ado
+ * (depth + 2 entries). */
+int heom_hier_info(const heom_hier *h, int64_t *n_ado, int64_t *level_offsets);
+
+/* Copy the tables into caller-owned host arrays of n_ado * n_modes entries, row u = ADO:
+ * tuples[u][l] = n_l, plus[u][l] = index of n + e_l or -1 (|n| = depth),
+ * minus[u][l] = index of n - e_l or -1 (n_l = 0).  Any pointer may be NULL. */
+int heom_hier_export(const heom_hier *h, uint8_t *tuples, int32_t *plus, int32_t *minus);
+
+/*
+ * heom_run_bytes -- device workspace bytes a run of this system, hierarchy and precision needs,
+ * including room for max_records observable records.  The hierarchy's n_modes must equal
+ * n_baths * (n_matsubara + 1).  Supported: 1 <= n_states <= 24.
+ */
+int heom_run_bytes(const heom_system *sys, const heom_hier *h, int precision, int64_t max_records,
+                   size_t *bytes);
+
+/*
+ * heom_run_create -- set up a propagation on the caller's device workspace (at least
+ * heom_run_bytes bytes, 256-byte aligned, on the current CUDA device) and stream (a
+ * cudaStream_t; NULL = the legacy default stream).  Computes the bath coefficients of Eq. HEOM
+ * (Matsubara gamma(b,k), c(b,k), the terminator and the rescaling factors) on the host in FP64,
+ * uploads the link tables, zeroes every ADO and writes sigma_0 = rho(0) (n_states x n_states,
+ * sigma0_im may be NULL).  dip_w (n_states weights w_a, or NULL) selects the dipole correlation
+ * sum_a w_a sigma_0[a][0] recorded with every observable record (Eq. lin_abs_mukamel with
+ * sigma_0(0) = mu^+|0><0|, state 0 the ground state).  Errors: HEOM_E_ARG, HEOM_E_NOMEM
+ * (workspace too small), HEOM_E_CUDA.  The workspace must stay allocated until
+ * heom_run_destroy.
+ */
+int heom_run_create(const heom_system *sys, const heom_hier *h, int precision, int64_t max_records,
+                    const double *sigma0_re, const double *sigma0_im, const double *dip_w,
+                    void *device_workspace, size_t workspace_bytes, void *cuda_stream, heom_run **out);
+int heom_run_destroy(heom_run *r);
+
+/*
+ * heom_propagate -- advance the whole hierarchy by n_steps steps of classic RK4 with step dt_fs
+ * (four evaluations of the right-hand side of Eq. HEOM per step).  Every obs_stride steps (0 =
+ * never) one observable record of sigma_0 is appended after the step.  Enqueued on the run's
+ * stream; does not block.  Errors: HEOM_E_ARG (dt_fs <= 0, n_steps < 0, dt_fs times the fastest
+ * decay rate D * max gamma above 2.5, where RK4 is no longer stable), HEOM_E_NOMEM (the records
+ * would overflow max_records), HEOM_E_CUDA.
+ */
+int heom_propagate(heom_run *r, double dt_fs, int64_t n_steps, int64_t obs_stride);
+
+/* Length in doubles of one observable record: n_states populations Re sigma_0[a][a], then
+ * Re Tr sigma_0, Im Tr sigma_0, Re C, Im C (C = sum_a w_a sigma_0[a][0], 0 without dip_w), then
+ * max_ij |sigma_0[i][j] - conj(sigma_0[j][i])|.  That is n_states + 5. */
+int heom_record_len(const heom_run *r);
+
+/*
+ * heom_observables -- synchronises the run's stream and copies up to cap_records records (the
+ * first record is the state at creation, then one per obs_stride steps) into out
+ * ([cap_records][heom_record_len]); *written = records copied.  HEOM_E_NUMERIC if a record
+ * holds NaN/Inf.
+ */
+int heom_observables(heom_run *r, double *out, int64_t cap_records, int64_t *written);
+
+/* Synchronises; copies sigma_0 (FP64) into caller host arrays of n_states^2 doubles. */
+int heom_get_sigma0(heom_run *r, double *re, double *im);
+
+/* Synchronises; copies ADOs [u0, u0 + count) of the current state into / out of caller host
+ * arrays [count][N][N] (FP32-stored ADOs are rounded on the way in).  HEOM_E_ARG if the range is
+ * outside [0, n_ado). */
+int heom_get_ados(heom_run *r, int64_t u0, int64_t count, double *re, double *im);
+int heom_set_ados(heom_run *r, int64_t u0, int64_t count, const double *re, const double *im);
+
+/*
+ * heom_rhs_eval -- evaluate the right-hand side of Eq. HEOM once on the current state with the
+ * same kernels heom_propagate uses, and copy ADOs [u0, u0 + count) of d sigma / dt into caller
+ * host arrays [count][N][N].  The state is not changed (the result goes through a scratch copy of
+ * the workspace).  Synchronises.
+ */
+int heom_rhs_eval(heom_run *r, int64_t u0, int64_t count, double *re, double *im);
+
+/* Number of ADOs, states and modes of a run; the step count and simulated time so far. */
+int heom_run_info(const heom_run *r, int64_t *n_ado, int *n_states, int *n_modes, int64_t *steps_done,
+                  double *t_fs);
+
+/* Kernel launches the library enqueued for this run since creation (all kinds). */
+int64_t heom_run_launches(const heom_run *r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEOM_H */

@@ -1,0 +1,705 @@
+// C ABI of libheom (include/heom.h): hierarchy handles, run set-up (units, Matsubara coefficients,
+// rescaling tables, workspace layout, table upload), the RK4 driver, observables and state I/O.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/heom.h"
+#include "heom_internal.h"
+
+namespace heom {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+int launch_stage(int precision, const StageCommon &c, double ch, const double *term, const double *H,
+                 const double *Hi, cudaStream_t st, int sm_count) {
+  if (c.u_end <= c.u_begin) return 0;
+  int rc;
+  if (precision == 0) {
+    rc = launch_stage_fp64_lo(c, ch, term, H, Hi, st, sm_count);
+    if (rc == 1) rc = launch_stage_fp64_hi(c, ch, term, H, Hi, st, sm_count);
+  } else if (precision == 1) {
+    rc = launch_stage_fp32_lo(c, ch, term, H, Hi, st, sm_count);
+    if (rc == 1) rc = launch_stage_fp32_hi(c, ch, term, H, Hi, st, sm_count);
+  } else {
+    rc = launch_stage_head_lo(c, ch, term, H, Hi, st, sm_count);
+    if (rc == 1) rc = launch_stage_head_hi(c, ch, term, H, Hi, st, sm_count);
+  }
+  if (rc == 1) {
+    set_error("stage kernel: n_states not compiled");
+    return -1;
+  }
+  return rc;
+}
+
+// 2 pi c in rad/fs per cm^-1 (c = 2.99792458e-5 cm/fs) and k_B in cm^-1/K (2019 SI, exact ratio).
+static const double kCmToRadFs = 2.0 * 3.14159265358979323846 * 2.99792458e-5;
+static const double kBoltzCm = 0.6950348004;
+
+}  // namespace heom
+
+using namespace heom;
+
+struct heom_hier {
+  Hierarchy h;
+};
+
+struct heom_run {
+  int precision = 0;
+  int n = 0, M = 0, D = 0, K = 0, B = 0;
+  int64_t n_ado = 0;
+  int u_split = 0;                   // ADOs stored in FP64 in the head region
+  int64_t head_pitch = 0, body_pitch = 0, u_pitch = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  // host copies of the per-run constants (rad/fs)
+  std::vector<double> H, Hi;         // shifted Re H, Im H
+  bool cplx_h = false;
+  std::vector<double> term;          // per state
+  double max_rate = 0;               // D * max gamma
+  // device
+  StateView y{}, zA{}, zB{};
+  int32_t *plusT = nullptr, *minusT = nullptr;
+  uint8_t *tupT = nullptr;
+  double *gsum = nullptr, *sp_tab = nullptr, *sm_tab = nullptr;
+  ModeDev *modes = nullptr;
+  int *state_mode_off = nullptr;
+  double *records = nullptr;         // [max_records][n + 5]
+  double *w_dev = nullptr;           // [n] dipole weights (zeros if none)
+  int64_t *rec_count = nullptr;      // device counter of records written
+  int64_t max_records = 0;
+  int64_t records_host = 0;          // records enqueued so far (host view)
+  int64_t steps_done = 0;
+  double t_fs = 0;
+  int64_t launches = 0;
+  size_t body_elem = 0;              // bytes per body complex element
+};
+
+extern "C" const char *heom_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------------------------------------
+// hierarchy handles
+
+extern "C" int heom_build_hierarchy(int n_modes, int depth, heom_hier **out) {
+  if (!out) { set_error("heom_build_hierarchy: out is NULL"); return HEOM_E_ARG; }
+  *out = nullptr;
+  heom_hier *h = new (std::nothrow) heom_hier;
+  if (!h) { set_error("heom_build_hierarchy: host allocation failed"); return HEOM_E_NOMEM; }
+  std::string err;
+  int rc = build_hierarchy(n_modes, depth, &h->h, &err);
+  if (rc != HEOM_OK) { delete h; set_error(err); return rc; }
+  *out = h;
+  return HEOM_OK;
+}
+
+extern "C" int heom_hier_destroy(heom_hier *h) {
+  delete h;
+  return HEOM_OK;
+}
+
+extern "C" int heom_hier_info(const heom_hier *h, int64_t *n_ado, int64_t *level_offsets) {
+  if (!h) { set_error("heom_hier_info: NULL handle"); return HEOM_E_ARG; }
+  if (n_ado) *n_ado = h->h.n;
+  if (level_offsets)
+    for (int L = 0; L <= h->h.D + 1; ++L) level_offsets[L] = h->h.level_off[L];
+  return HEOM_OK;
+}
+
+extern "C" int heom_hier_export(const heom_hier *h, uint8_t *tuples, int32_t *plus, int32_t *minus) {
+  if (!h) { set_error("heom_hier_export: NULL handle"); return HEOM_E_ARG; }
+  const size_t cnt = (size_t)h->h.n * h->h.M;
+  if (tuples) memcpy(tuples, h->h.tuples.data(), cnt);
+  if (plus) memcpy(plus, h->h.plus.data(), cnt * sizeof(int32_t));
+  if (minus) memcpy(minus, h->h.minus.data(), cnt * sizeof(int32_t));
+  return HEOM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// run set-up
+
+namespace {
+
+struct Layout {
+  size_t off_plus, off_minus, off_tup, off_gsum, off_sp, off_sm, off_modes, off_smo, off_rec, off_w, off_cnt;
+  size_t off_state[3];
+  size_t head_bytes, body_bytes;
+  size_t total;
+};
+
+inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int check_system(const heom_system *s, const heom_hier *h, int precision) {
+  if (!s || !h) { set_error("NULL system or hierarchy"); return HEOM_E_ARG; }
+  if (s->n_states < 1 || s->n_states > kMaxStates) {
+    set_error("n_states must be in [1, 24]");
+    return HEOM_E_ARG;
+  }
+  if (!s->H_re) { set_error("H_re is NULL"); return HEOM_E_ARG; }
+  if (s->n_baths < 1 || !s->bath_state || !s->lambda_cm || !s->tau_fs || !s->T_K || s->n_matsubara < 0) {
+    set_error("need n_baths >= 1, bath arrays and n_matsubara >= 0");
+    return HEOM_E_ARG;
+  }
+  if ((int64_t)s->n_baths * (s->n_matsubara + 1) != h->h.M) {
+    set_error("hierarchy n_modes != n_baths * (n_matsubara + 1)");
+    return HEOM_E_ARG;
+  }
+  for (int b = 0; b < s->n_baths; ++b) {
+    if (s->bath_state[b] < 0 || s->bath_state[b] >= s->n_states) {
+      set_error("bath_state out of range");
+      return HEOM_E_ARG;
+    }
+    if (!(s->tau_fs[b] > 0) || !(s->T_K[b] > 0) || !(s->lambda_cm[b] >= 0)) {
+      set_error("need tau_fs > 0, T_K > 0, lambda_cm >= 0");
+      return HEOM_E_ARG;
+    }
+  }
+  if (precision != HEOM_FP64 && precision != HEOM_FP32_MIXED) {
+    set_error("unknown precision");
+    return HEOM_E_ARG;
+  }
+  return HEOM_OK;
+}
+
+Layout make_layout(int n, int M, int D, int64_t n_ado, int u_split, int precision, int64_t max_records,
+                   int64_t *head_pitch, int64_t *body_pitch, int64_t *u_pitch) {
+  Layout L{};
+  const int64_t E = (int64_t)n * n;
+  *u_pitch = (n_ado + 63) / 64 * 64;
+  *head_pitch = (u_split + 63) / 64 * 64;
+  const int64_t nb = n_ado - u_split;
+  *body_pitch = (nb + 63) / 64 * 64;
+  const size_t be = (precision == HEOM_FP64) ? sizeof(double2) : sizeof(float2);
+  size_t o = 0;
+  L.off_plus = o; o = al(o + (size_t)M * *u_pitch * sizeof(int32_t));
+  L.off_minus = o; o = al(o + (size_t)M * *u_pitch * sizeof(int32_t));
+  L.off_tup = o; o = al(o + (size_t)M * *u_pitch);
+  L.off_gsum = o; o = al(o + (size_t)*u_pitch * sizeof(double));
+  L.off_sp = o; o = al(o + (size_t)M * (D + 1) * sizeof(double));
+  L.off_sm = o; o = al(o + (size_t)M * (D + 1) * sizeof(double));
+  L.off_modes = o; o = al(o + (size_t)M * sizeof(ModeDev));
+  L.off_smo = o; o = al(o + (size_t)(n + 1) * sizeof(int));
+  L.off_rec = o; o = al(o + (size_t)std::max<int64_t>(max_records, 1) * (n + 5) * sizeof(double));
+  L.off_w = o; o = al(o + (size_t)n * sizeof(double));
+  L.off_cnt = o; o = al(o + sizeof(int64_t));
+  L.head_bytes = al((size_t)E * *head_pitch * sizeof(double2));
+  L.body_bytes = al((size_t)E * *body_pitch * be);
+  for (int c = 0; c < 3; ++c) {
+    L.off_state[c] = o;
+    o = al(o + L.head_bytes + L.body_bytes);
+  }
+  L.total = o;
+  return L;
+}
+
+int cuda_fail(const char *what, cudaError_t e) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return HEOM_E_CUDA;
+}
+
+}  // namespace
+
+extern "C" int heom_run_bytes(const heom_system *sys, const heom_hier *h, int precision, int64_t max_records,
+                              size_t *bytes) {
+  int rc = check_system(sys, h, precision);
+  if (rc) return rc;
+  if (!bytes || max_records < 0) { set_error("heom_run_bytes: bad output pointer or max_records"); return HEOM_E_ARG; }
+  int64_t hp, bp, up;
+  const int u_split = (precision == HEOM_FP64) ? 0 : (int)std::min<int64_t>(h->h.n, h->h.level_off[std::min(2, h->h.D + 1)]);
+  Layout L = make_layout(sys->n_states, h->h.M, h->h.D, h->h.n, u_split, precision, max_records, &hp, &bp, &up);
+  *bytes = L.total;
+  return HEOM_OK;
+}
+
+namespace heom {
+__global__ void record_kernel(StateView y, int64_t hp, int64_t bp, int u_split, int n, const double *w,
+                              double *records, int64_t *rec_count, int64_t max_records, int is_fp64_body);
+__global__ void scatter_kernel(StateView dst, int64_t hp, int64_t bp, int u_split, int body_fp32, int n, int64_t u0,
+                               int64_t count, const double *re, const double *im);
+__global__ void gather_kernel(StateView src, int64_t hp, int64_t bp, int u_split, int body_fp32, int n, int64_t u0,
+                              int64_t count, double *re, double *im);
+}  // namespace heom
+
+static StateView view_at(char *base, const Layout &L, int c) {
+  StateView v;
+  v.head = reinterpret_cast<double2 *>(base + L.off_state[c]);
+  v.body = base + L.off_state[c] + L.head_bytes;
+  return v;
+}
+
+static int enqueue_record(heom_run *r) {
+  if (r->records_host >= r->max_records) {
+    set_error("observable record buffer full (max_records)");
+    return HEOM_E_NOMEM;
+  }
+  record_kernel<<<1, 32, 0, r->stream>>>(r->y, r->head_pitch, r->body_pitch, r->u_split, r->n, r->w_dev, r->records,
+                                         r->rec_count, r->max_records, r->precision == HEOM_FP64);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("record kernel launch", e);
+  ++r->records_host;
+  ++r->launches;
+  return HEOM_OK;
+}
+
+extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int precision, int64_t max_records,
+                               const double *sigma0_re, const double *sigma0_im, const double *dip_w,
+                               void *device_workspace, size_t workspace_bytes, void *cuda_stream, heom_run **out) {
+  if (!out) { set_error("heom_run_create: out is NULL"); return HEOM_E_ARG; }
+  *out = nullptr;
+  int rc = check_system(sys, hh, precision);
+  if (rc) return rc;
+  if (!sigma0_re || max_records < 1) { set_error("heom_run_create: need sigma0_re and max_records >= 1"); return HEOM_E_ARG; }
+  if (!device_workspace || (reinterpret_cast<uintptr_t>(device_workspace) & 255)) {
+    set_error("heom_run_create: workspace must be a 256-byte aligned device pointer");
+    return HEOM_E_ARG;
+  }
+  const Hierarchy &h = hh->h;
+  const int n = sys->n_states, M = h.M, D = h.D, K = sys->n_matsubara, B = sys->n_baths;
+  heom_run *r = new (std::nothrow) heom_run;
+  if (!r) { set_error("host allocation failed"); return HEOM_E_NOMEM; }
+  r->precision = precision;
+  r->n = n; r->M = M; r->D = D; r->K = K; r->B = B;
+  r->n_ado = h.n;
+  r->u_split = (precision == HEOM_FP64) ? 0 : (int)std::min<int64_t>(h.n, h.level_off[std::min(2, D + 1)]);
+  r->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  r->max_records = max_records;
+  Layout L = make_layout(n, M, D, h.n, r->u_split, precision, max_records, &r->head_pitch, &r->body_pitch, &r->u_pitch);
+  if (workspace_bytes < L.total) {
+    delete r;
+    set_error("workspace too small: need " + std::to_string(L.total) + " bytes");
+    return HEOM_E_NOMEM;
+  }
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&r->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (ce != cudaSuccess) { delete r; return cuda_fail("device query", ce); }
+
+  // ---- units and Hamiltonian: H in rad/fs, shifted by h0 = (max + min)/2 of Re diag (exact for
+  // the commutator, the only place H enters) to keep the products small in FP32.
+  double dmax = -1e300, dmin = 1e300;
+  for (int i = 0; i < n; ++i) {
+    dmax = std::max(dmax, sys->H_re[i * n + i]);
+    dmin = std::min(dmin, sys->H_re[i * n + i]);
+  }
+  const double h0 = 0.5 * (dmax + dmin);
+  r->H.assign((size_t)n * n, 0.0);
+  r->Hi.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n * n; ++i) {
+    r->H[i] = kCmToRadFs * (sys->H_re[i] - ((i / n == i % n) ? h0 : 0.0));
+    r->Hi[i] = sys->H_im ? kCmToRadFs * sys->H_im[i] : 0.0;
+    if (r->Hi[i] != 0.0) r->cplx_h = true;
+  }
+
+  // ---- Matsubara coefficients of Eq. HEOM (Drude-Lorentz, Omega = 0), terminator and rescaling
+  std::vector<double> gam(M), cc(M), lnu(M);
+  std::vector<int> mstate(M);
+  r->term.assign(n, 0.0);
+  double gmax = 0;
+  for (int b = 0; b < B; ++b) {
+    const double lam = kCmToRadFs * sys->lambda_cm[b];
+    const double nu = 1.0 / sys->tau_fs[b];
+    const double beta = 1.0 / (kCmToRadFs * kBoltzCm * sys->T_K[b]);
+    double csum = 0;
+    for (int k = 0; k <= K; ++k) {
+      const int l = b * (K + 1) + k;
+      double g, c;
+      if (k == 0) {
+        g = nu;
+        c = lam * nu / std::tan(0.5 * beta * nu);
+      } else {
+        g = 2.0 * 3.14159265358979323846 * k / beta;
+        if (std::fabs(g * g - nu * nu) < 1e-6 * g * g) {
+          delete r;
+          set_error("Matsubara frequency gamma_k equals nu for a bath (c_k diverges)");
+          return HEOM_E_ARG;
+        }
+        c = 4.0 * lam * nu / beta * g / (g * g - nu * nu);
+      }
+      gam[l] = g;
+      cc[l] = c;
+      lnu[l] = (k == 0) ? lam * nu : 0.0;
+      mstate[l] = sys->bath_state[b];
+      csum += c / g;
+      gmax = std::max(gmax, g);
+    }
+    if (sys->terminator) r->term[sys->bath_state[b]] += 2.0 * lam / (beta * nu) - csum;
+  }
+  r->max_rate = D * gmax;
+
+  // modes grouped by state (stable), the order the kernel walks them
+  std::vector<int> perm(M);
+  for (int l = 0; l < M; ++l) perm[l] = l;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b2) { return mstate[a] < mstate[b2]; });
+  std::vector<int> smo(n + 1, 0);
+  for (int l = 0; l < M; ++l) smo[mstate[l] + 1]++;
+  for (int s = 0; s < n; ++s) smo[s + 1] += smo[s];
+  std::vector<ModeDev> md(M);
+  std::vector<double> sp((size_t)M * (D + 1)), sm((size_t)M * (D + 1));
+  for (int q = 0; q < M; ++q) {
+    const int l = perm[q];
+    md[q].state = mstate[l];
+    md[q].pad = 0;
+    md[q].c = cc[l];
+    md[q].lamnu = lnu[l];
+    const double ac = std::fabs(cc[l]);
+    for (int nl = 0; nl <= D; ++nl) {
+      const bool scaled = sys->rescale && ac >= 1e-300;
+      sp[(size_t)q * (D + 1) + nl] = scaled ? std::sqrt((nl + 1) * ac) : 1.0;
+      sm[(size_t)q * (D + 1) + nl] = scaled ? std::sqrt(nl / ac) : (double)nl;
+    }
+  }
+
+  // ---- tables, transposed to [q][u] so consecutive ADOs are contiguous
+  std::vector<int32_t> plusT, minusT;
+  std::vector<uint8_t> tupT;
+  std::vector<double> gs(r->u_pitch, 0.0);
+  try {
+    plusT.assign((size_t)M * r->u_pitch, -1);
+    minusT.assign((size_t)M * r->u_pitch, -1);
+    tupT.assign((size_t)M * r->u_pitch, 0);
+  } catch (...) {
+    delete r;
+    set_error("host allocation failed (tables)");
+    return HEOM_E_NOMEM;
+  }
+  for (int64_t u = 0; u < h.n; ++u) {
+    double g = 0;
+    for (int l = 0; l < M; ++l) g += h.tuples[(size_t)u * M + l] * gam[l];
+    gs[u] = g;
+    for (int q = 0; q < M; ++q) {
+      const int l = perm[q];
+      plusT[(size_t)q * r->u_pitch + u] = h.plus[(size_t)u * M + l];
+      minusT[(size_t)q * r->u_pitch + u] = h.minus[(size_t)u * M + l];
+      tupT[(size_t)q * r->u_pitch + u] = h.tuples[(size_t)u * M + l];
+    }
+  }
+
+  char *base = reinterpret_cast<char *>(device_workspace);
+  r->plusT = reinterpret_cast<int32_t *>(base + L.off_plus);
+  r->minusT = reinterpret_cast<int32_t *>(base + L.off_minus);
+  r->tupT = reinterpret_cast<uint8_t *>(base + L.off_tup);
+  r->gsum = reinterpret_cast<double *>(base + L.off_gsum);
+  r->sp_tab = reinterpret_cast<double *>(base + L.off_sp);
+  r->sm_tab = reinterpret_cast<double *>(base + L.off_sm);
+  r->modes = reinterpret_cast<ModeDev *>(base + L.off_modes);
+  r->state_mode_off = reinterpret_cast<int *>(base + L.off_smo);
+  r->records = reinterpret_cast<double *>(base + L.off_rec);
+  r->w_dev = reinterpret_cast<double *>(base + L.off_w);
+  r->rec_count = reinterpret_cast<int64_t *>(base + L.off_cnt);
+  r->y = view_at(base, L, 0);
+  r->zA = view_at(base, L, 1);
+  r->zB = view_at(base, L, 2);
+
+  std::vector<double> w(n, 0.0);
+  if (dip_w) for (int i = 0; i < n; ++i) w[i] = dip_w[i];
+  cudaStream_t st = r->stream;
+  ce = cudaMemcpyAsync(r->plusT, plusT.data(), plusT.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->minusT, minusT.data(), minusT.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->tupT, tupT.data(), tupT.size(), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->gsum, gs.data(), gs.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->sp_tab, sp.data(), sp.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->sm_tab, sm.data(), sm.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->modes, md.data(), md.size() * sizeof(ModeDev), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->state_mode_off, smo.data(), smo.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->w_dev, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(r->rec_count, 0, sizeof(int64_t), st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(base + L.off_state[0], 0, L.head_bytes + L.body_bytes, st);
+  // the host vectors above are pageable: the copies complete before cudaMemcpyAsync returns
+  if (ce != cudaSuccess) { delete r; return cuda_fail("workspace upload", ce); }
+  // sigma_0 = rho(0): ADO 0 through the host-layout path
+  std::vector<double> s0r((size_t)n * n), s0i((size_t)n * n, 0.0);
+  for (int i = 0; i < n * n; ++i) { s0r[i] = sigma0_re[i]; if (sigma0_im) s0i[i] = sigma0_im[i]; }
+  *out = r;
+  rc = heom_set_ados(r, 0, 1, s0r.data(), s0i.data());
+  if (rc == HEOM_OK) rc = enqueue_record(r);
+  if (rc != HEOM_OK) { *out = nullptr; delete r; return rc; }
+  return HEOM_OK;
+}
+
+extern "C" int heom_run_destroy(heom_run *r) {
+  delete r;
+  return HEOM_OK;
+}
+
+extern "C" int heom_record_len(const heom_run *r) { return r ? r->n + 5 : 0; }
+
+// ------------------------------------------------------------------------------------------------
+// propagation: classic RK4 of a linear, time-independent right-hand side, evaluated in Horner form
+//   y_{t+h} = y + h L (y + h/2 L (y + h/3 L (y + h/4 L y)))
+// which is the same degree-4 polynomial as the four-stage classic tableau and needs three state
+// copies (y, zA, zB) instead of four.
+
+static StageCommon common_for(const heom_run *r, StateView zin, StateView y, StateView out) {
+  StageCommon c{};
+  c.zin = zin;
+  c.y = y;
+  c.out = out;
+  c.plusT = r->plusT;
+  c.minusT = r->minusT;
+  c.tupT = r->tupT;
+  c.gsum = r->gsum;
+  c.modes = r->modes;
+  c.state_mode_off = r->state_mode_off;
+  c.sp_tab = r->sp_tab;
+  c.sm_tab = r->sm_tab;
+  c.head_pitch = r->head_pitch;
+  c.body_pitch = r->body_pitch;
+  c.u_pitch = r->u_pitch;
+  c.u_split = r->u_split;
+  c.n_ado = (int)r->n_ado;
+  c.n = r->n;
+  c.M = r->M;
+  c.D = r->D;
+  c.cplx_h = r->cplx_h ? 1 : 0;
+  return c;
+}
+
+static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, double ch) {
+  StageCommon c = common_for(r, zin, y, out);
+  const double *Hi = r->cplx_h ? r->Hi.data() : nullptr;
+  int rc;
+  if (r->precision == HEOM_FP64) {
+    c.u_begin = 0;
+    c.u_end = (int)r->n_ado;
+    rc = launch_stage(0, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
+    if (rc) return HEOM_E_CUDA;
+    ++r->launches;
+    return HEOM_OK;
+  }
+  // mixed: FP64 head (levels 0, 1) and FP32 body
+  c.u_begin = 0;
+  c.u_end = r->u_split;
+  rc = launch_stage(2, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
+  if (rc) return HEOM_E_CUDA;
+  ++r->launches;
+  c.u_begin = r->u_split;
+  c.u_end = (int)r->n_ado;
+  if (c.u_end > c.u_begin) {
+    rc = launch_stage(1, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
+    if (rc) return HEOM_E_CUDA;
+    ++r->launches;
+  }
+  return HEOM_OK;
+}
+
+extern "C" int heom_propagate(heom_run *r, double dt_fs, int64_t n_steps, int64_t obs_stride) {
+  if (!r) { set_error("heom_propagate: NULL run"); return HEOM_E_ARG; }
+  if (!(dt_fs > 0) || n_steps < 0 || obs_stride < 0) {
+    set_error("heom_propagate: need dt_fs > 0, n_steps >= 0, obs_stride >= 0");
+    return HEOM_E_ARG;
+  }
+  if (dt_fs * r->max_rate > 2.5) {
+    set_error("heom_propagate: dt_fs * depth * max gamma > 2.5 (RK4 unstable; the paper asks dt << 1/gamma_k)");
+    return HEOM_E_ARG;
+  }
+  if (obs_stride > 0) {
+    const int64_t first = obs_stride - (r->steps_done % obs_stride);
+    const int64_t need = (n_steps >= first) ? 1 + (n_steps - first) / obs_stride : 0;
+    if (r->records_host + need > r->max_records) {
+      set_error("heom_propagate: observable records would exceed max_records");
+      return HEOM_E_NOMEM;
+    }
+  }
+  const double h = dt_fs;
+  StateView none{nullptr, nullptr};
+  (void)none;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    int rc;
+    if ((rc = run_stage(r, r->y, r->y, r->zA, h / 4))) return rc;
+    if ((rc = run_stage(r, r->zA, r->y, r->zB, h / 3))) return rc;
+    if ((rc = run_stage(r, r->zB, r->y, r->zA, h / 2))) return rc;
+    if ((rc = run_stage(r, r->zA, r->y, r->y, h))) return rc;
+    ++r->steps_done;
+    r->t_fs += h;
+    if (obs_stride > 0 && r->steps_done % obs_stride == 0)
+      if ((rc = enqueue_record(r))) return rc;
+  }
+  return HEOM_OK;
+}
+
+extern "C" int heom_observables(heom_run *r, double *out, int64_t cap_records, int64_t *written) {
+  if (!r || !out || cap_records < 0) { set_error("heom_observables: bad arguments"); return HEOM_E_ARG; }
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail("heom_observables: stream", e);
+  int64_t cnt = 0;
+  e = cudaMemcpy(&cnt, r->rec_count, sizeof(int64_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail("heom_observables: counter", e);
+  cnt = std::min(cnt, cap_records);
+  const int rl = r->n + 5;
+  if (cnt > 0) {
+    e = cudaMemcpy(out, r->records, (size_t)cnt * rl * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail("heom_observables: copy", e);
+  }
+  if (written) *written = cnt;
+  for (int64_t i = 0; i < cnt * rl; ++i)
+    if (!std::isfinite(out[i])) {
+      set_error("heom_observables: NaN/Inf in the root ADO");
+      return HEOM_E_NUMERIC;
+    }
+  return HEOM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// state I/O through the host layout [count][N][N]; zB is the staging area.
+
+static int64_t staging_ados(const heom_run *r) {
+  // zB holds (head + body) bytes; every staged ADO needs 2 * N^2 doubles
+  const size_t bytes = (size_t)(r->n * r->n) * (r->head_pitch * sizeof(double2) +
+                                                r->body_pitch * (r->precision == HEOM_FP64 ? 16 : 8));
+  return std::max<int64_t>(1, (int64_t)(bytes / (2 * sizeof(double) * r->n * r->n)));
+}
+
+static int io_range(heom_run *r, StateView state, int64_t u0, int64_t count, double *re, double *im, bool to_device) {
+  if (!r || u0 < 0 || count < 0 || u0 + count > r->n_ado || (count > 0 && (!re || !im))) {
+    set_error("ADO range outside the hierarchy or NULL buffer");
+    return HEOM_E_ARG;
+  }
+  const int64_t E = (int64_t)r->n * r->n;
+  const int64_t chunk = staging_ados(r);
+  double *st_re = reinterpret_cast<double *>(r->zB.head);
+  for (int64_t c0 = 0; c0 < count; c0 += chunk) {
+    const int64_t cc = std::min(chunk, count - c0);
+    double *st_im = st_re + cc * E;
+    cudaError_t e;
+    if (to_device) {
+      e = cudaMemcpyAsync(st_re, re + c0 * E, cc * E * sizeof(double), cudaMemcpyHostToDevice, r->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(st_im, im + c0 * E, cc * E * sizeof(double), cudaMemcpyHostToDevice, r->stream);
+      if (e != cudaSuccess) return cuda_fail("state upload", e);
+      const int blocks = (int)std::min<int64_t>((cc * E + 255) / 256, 65535);
+      scatter_kernel<<<blocks, 256, 0, r->stream>>>(state, r->head_pitch, r->body_pitch, r->u_split,
+                                                   r->precision != HEOM_FP64, r->n, u0 + c0, cc, st_re, st_im);
+      ++r->launches;
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail("scatter kernel", e);
+      e = cudaStreamSynchronize(r->stream);  // the staging area is reused by the next chunk
+      if (e != cudaSuccess) return cuda_fail("state upload sync", e);
+    } else {
+      const int blocks = (int)std::min<int64_t>((cc * E + 255) / 256, 65535);
+      gather_kernel<<<blocks, 256, 0, r->stream>>>(state, r->head_pitch, r->body_pitch, r->u_split,
+                                                  r->precision != HEOM_FP64, r->n, u0 + c0, cc, st_re, st_im);
+      ++r->launches;
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail("gather kernel", e);
+      e = cudaMemcpyAsync(re + c0 * E, st_re, cc * E * sizeof(double), cudaMemcpyDeviceToHost, r->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(im + c0 * E, st_im, cc * E * sizeof(double), cudaMemcpyDeviceToHost, r->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+      if (e != cudaSuccess) return cuda_fail("state download", e);
+    }
+  }
+  return HEOM_OK;
+}
+
+extern "C" int heom_set_ados(heom_run *r, int64_t u0, int64_t count, const double *re, const double *im) {
+  if (!r) { set_error("heom_set_ados: NULL run"); return HEOM_E_ARG; }
+  return io_range(r, r->y, u0, count, const_cast<double *>(re), const_cast<double *>(im), true);
+}
+
+extern "C" int heom_get_ados(heom_run *r, int64_t u0, int64_t count, double *re, double *im) {
+  if (!r) { set_error("heom_get_ados: NULL run"); return HEOM_E_ARG; }
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail("heom_get_ados: stream", e);
+  return io_range(r, r->y, u0, count, re, im, false);
+}
+
+extern "C" int heom_get_sigma0(heom_run *r, double *re, double *im) { return heom_get_ados(r, 0, 1, re, im); }
+
+extern "C" int heom_rhs_eval(heom_run *r, int64_t u0, int64_t count, double *re, double *im) {
+  if (!r) { set_error("heom_rhs_eval: NULL run"); return HEOM_E_ARG; }
+  StateView none{nullptr, nullptr};
+  int rc = run_stage(r, r->y, none, r->zA, 1.0);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail("heom_rhs_eval: stream", e);
+  return io_range(r, r->zA, u0, count, re, im, false);
+}
+
+extern "C" int heom_run_info(const heom_run *r, int64_t *n_ado, int *n_states, int *n_modes, int64_t *steps_done,
+                             double *t_fs) {
+  if (!r) { set_error("heom_run_info: NULL run"); return HEOM_E_ARG; }
+  if (n_ado) *n_ado = r->n_ado;
+  if (n_states) *n_states = r->n;
+  if (n_modes) *n_modes = r->M;
+  if (steps_done) *steps_done = r->steps_done;
+  if (t_fs) *t_fs = r->t_fs;
+  return HEOM_OK;
+}
+
+extern "C" int64_t heom_run_launches(const heom_run *r) { return r ? r->launches : -1; }
+
+// ------------------------------------------------------------------------------------------------
+// small kernels
+
+namespace heom {
+
+__device__ __forceinline__ double2 ld_any(const StateView &s, int64_t hp, int64_t bp, int u_split, int body_fp32,
+                                          int64_t e, int64_t v) {
+  if (v < u_split) return s.head[e * hp + v];
+  if (body_fp32) {
+    float2 f = reinterpret_cast<const float2 *>(s.body)[e * bp + (v - u_split)];
+    return make_double2(f.x, f.y);
+  }
+  return reinterpret_cast<const double2 *>(s.body)[e * bp + (v - u_split)];
+}
+
+// One observable record of sigma_0 (FP64): populations, trace, dipole correlation, Hermiticity.
+__global__ void record_kernel(StateView y, int64_t hp, int64_t bp, int u_split, int n, const double *w,
+                              double *records, int64_t *rec_count, int64_t max_records, int is_fp64_body) {
+  if (threadIdx.x != 0) return;
+  const int64_t idx = *rec_count;
+  if (idx >= max_records) return;
+  double *rec = records + idx * (n + 5);
+  double tr = 0, ti = 0, cr = 0, ci = 0, herm = 0;
+  for (int a = 0; a < n; ++a) {
+    const double2 d = ld_any(y, hp, bp, u_split, !is_fp64_body, (int64_t)a * n + a, 0);
+    rec[a] = d.x;
+    tr += d.x;
+    ti += d.y;
+    const double2 c0 = ld_any(y, hp, bp, u_split, !is_fp64_body, (int64_t)a * n, 0);
+    cr += w[a] * c0.x;
+    ci += w[a] * c0.y;
+    for (int b = 0; b < n; ++b) {
+      const double2 x = ld_any(y, hp, bp, u_split, !is_fp64_body, (int64_t)a * n + b, 0);
+      const double2 z = ld_any(y, hp, bp, u_split, !is_fp64_body, (int64_t)b * n + a, 0);
+      herm = fmax(herm, hypot(x.x - z.x, x.y + z.y));
+    }
+  }
+  rec[n] = tr;
+  rec[n + 1] = ti;
+  rec[n + 2] = cr;
+  rec[n + 3] = ci;
+  rec[n + 4] = herm;
+  *rec_count = idx + 1;
+}
+
+__global__ void scatter_kernel(StateView dst, int64_t hp, int64_t bp, int u_split, int body_fp32, int n, int64_t u0,
+                               int64_t count, const double *re, const double *im) {
+  const int64_t E = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count * E; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / E, e = t - c * E;
+    const int64_t v = u0 + c;
+    if (v < u_split) {
+      dst.head[e * hp + v] = make_double2(re[t], im[t]);
+    } else if (body_fp32) {
+      reinterpret_cast<float2 *>(dst.body)[e * bp + (v - u_split)] = make_float2((float)re[t], (float)im[t]);
+    } else {
+      reinterpret_cast<double2 *>(dst.body)[e * bp + (v - u_split)] = make_double2(re[t], im[t]);
+    }
+  }
+}
+
+__global__ void gather_kernel(StateView src, int64_t hp, int64_t bp, int u_split, int body_fp32, int n, int64_t u0,
+                              int64_t count, double *re, double *im) {
+  const int64_t E = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count * E; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / E, e = t - c * E;
+    const double2 d = ld_any(src, hp, bp, u_split, body_fp32, e, u0 + c);
+    re[t] = d.x;
+    im[t] = d.y;
+  }
+}
+
+}  // namespace heom

@@ -1,0 +1,81 @@
+// Internal declarations shared by the CUDA translation units of libheom (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hierarchy.h"
+
+namespace heom {
+
+constexpr int kMaxStates = 24;
+constexpr int kStageWarps = 4;  // warps per CTA of the stage kernel
+
+void set_error(const std::string &msg);
+
+// Per-mode constants, one record per mode l = b * (K + 1) + k, grouped by state on the device.
+struct ModeDev {
+  int state;      // s_l, the state coupled to the mode's bath
+  int pad;
+  double c;       // c(b, k), real
+  double lamnu;   // lambda_b nu_b for k = 0, else 0
+};
+
+// Hierarchy state storage of one RK4 copy: ADOs u < u_split ("head") as FP64 complex, ADOs
+// u >= u_split ("body") as complex of the run's storage type; both element-major, so element e of
+// ADOs u, u+1, ... is contiguous: head[e * head_pitch + u], body[e * body_pitch + (u - u_split)].
+struct StateView {
+  double2 *head;
+  void *body;
+};
+
+// Everything a stage launch needs besides H, passed by value in the kernel parameters.
+struct StageCommon {
+  StateView zin;        // state the RHS is evaluated on (own tile and neighbour gathers)
+  StateView y;          // Horner base y (head == nullptr && body == nullptr: none)
+  StateView out;        // result y + ch * L zin (or ch * L zin)
+  const int32_t *plusT; // [M][u_pitch]
+  const int32_t *minusT;
+  const uint8_t *tupT;  // [M][u_pitch]
+  const double *gsum;   // [u_pitch] sum_l n_l gamma_l
+  const ModeDev *modes; // [M], ordered by state
+  const int *state_mode_off;  // [n + 1] modes of state s: [off[s], off[s+1])
+  const double *sp_tab;       // [M][D + 1] up factor  s+_l(n_l)
+  const double *sm_tab;       // [M][D + 1] down factor s-_l(n_l)
+  int64_t head_pitch, body_pitch, u_pitch;
+  int u_split, n_ado;
+  int u_begin, u_end;   // ADO range of this launch
+  int n, M, D;
+  int cplx_h;           // H has an imaginary part
+};
+
+template <typename CT>
+struct StageArgs {
+  StageCommon c;
+  CT ch;                      // Horner coefficient times h (1 for a bare RHS evaluation)
+  CT term[kMaxStates];        // terminator Delta per state (0 if none)
+  CT H[kMaxStates * kMaxStates];   // Re H - h0 I, row stride kMaxStates, rad/fs
+  CT Hi[kMaxStates * kMaxStates];  // Im H
+};
+
+// Stage launchers, one per storage combination and range of n (stage_*.cu); each returns 0 on
+// success, 1 if n is not compiled in that unit, negative on error.
+#define HEOM_DECLARE_LAUNCH(NAME)                                                                      \
+  int NAME(const StageCommon &c, double ch, const double *term, const double *H, const double *Hi, \
+           cudaStream_t st, int sm_count);
+HEOM_DECLARE_LAUNCH(launch_stage_fp64_lo)
+HEOM_DECLARE_LAUNCH(launch_stage_fp64_hi)
+HEOM_DECLARE_LAUNCH(launch_stage_fp32_lo)
+HEOM_DECLARE_LAUNCH(launch_stage_fp32_hi)
+HEOM_DECLARE_LAUNCH(launch_stage_head_lo)
+HEOM_DECLARE_LAUNCH(launch_stage_head_hi)
+#undef HEOM_DECLARE_LAUNCH
+
+// precision: 0 = FP64 (compute and storage double), 1 = mixed body (float, float), 2 = mixed head
+// (compute double, body storage float).
+int launch_stage(int precision, const StageCommon &c, double ch, const double *term, const double *H,
+                 const double *Hi, cudaStream_t st, int sm_count);
+
+}  // namespace heom

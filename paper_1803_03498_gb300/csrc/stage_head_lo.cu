@@ -1,0 +1,25 @@
+// Instantiations of the stage kernel: compute double, storage float, n_states in {2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12}.
+#include "stage_kernel.cuh"
+
+namespace heom {
+
+int launch_stage_head_lo(const StageCommon &c, double ch, const double *term, const double *H, const double *Hi,
+                        cudaStream_t st, int sm_count) {
+  switch (nm_for(c.n)) {
+    case 2: return launch_nm<2, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 3: return launch_nm<3, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 4: return launch_nm<4, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 5: return launch_nm<5, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 6: return launch_nm<6, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 7: return launch_nm<7, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 8: return launch_nm<8, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 9: return launch_nm<9, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 10: return launch_nm<10, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 11: return launch_nm<11, double, float>(c, ch, term, H, Hi, st, sm_count);
+    case 12: return launch_nm<12, double, float>(c, ch, term, H, Hi, st, sm_count);
+    default:
+      return 1;  // not in this translation unit
+  }
+}
+
+}  // namespace heom

@@ -1,0 +1,246 @@
+"""Thin Python binding of libheom's C ABI (include/heom.h): argument marshalling only.
+
+Every step of the propagation runs in the CUDA library; this module converts numpy arrays to
+pointers, takes device memory for the workspace from PyTorch's caching allocator and passes the
+current torch CUDA stream.  There is no fallback: ``load()`` raises if ``libheom.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libheom.so")
+
+HEOM_OK = 0
+HEOM_E_ARG, HEOM_E_OVERFLOW, HEOM_E_NOMEM, HEOM_E_CUDA, HEOM_E_TIMEOUT, HEOM_E_NUMERIC, HEOM_E_STATE = range(-1, -8, -1)
+FP64, FP32_MIXED = 0, 1
+PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
+
+# every symbol include/heom.h declares
+ABI_SYMBOLS = [
+    "heom_last_error", "heom_build_hierarchy", "heom_hier_destroy", "heom_hier_info", "heom_hier_export",
+    "heom_run_bytes", "heom_run_create", "heom_run_destroy", "heom_propagate", "heom_record_len",
+    "heom_observables", "heom_get_sigma0", "heom_get_ados", "heom_set_ados", "heom_rhs_eval", "heom_run_info",
+    "heom_run_launches",
+]
+
+
+class HeomError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libheom error {code}: {msg}")
+        self.code = code
+
+
+class _System(ctypes.Structure):
+    _fields_ = [
+        ("n_states", ctypes.c_int),
+        ("H_re", ctypes.POINTER(ctypes.c_double)),
+        ("H_im", ctypes.POINTER(ctypes.c_double)),
+        ("n_baths", ctypes.c_int),
+        ("bath_state", ctypes.POINTER(ctypes.c_int)),
+        ("lambda_cm", ctypes.POINTER(ctypes.c_double)),
+        ("tau_fs", ctypes.POINTER(ctypes.c_double)),
+        ("T_K", ctypes.POINTER(ctypes.c_double)),
+        ("n_matsubara", ctypes.c_int),
+        ("terminator", ctypes.c_int),
+        ("rescale", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libheom.so (built by ``paper_1803_03498_gb300.build.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libheom.so not found at {LIB_PATH}: build it with paper_1803_03498_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    i, i64, d, vp, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+    L.heom_last_error.restype = ctypes.c_char_p
+    L.heom_last_error.argtypes = []
+    L.heom_build_hierarchy.argtypes = [i, i, P(vp)]
+    L.heom_hier_destroy.argtypes = [vp]
+    L.heom_hier_info.argtypes = [vp, P(i64), P(i64)]
+    L.heom_hier_export.argtypes = [vp, P(ctypes.c_uint8), P(ctypes.c_int32), P(ctypes.c_int32)]
+    L.heom_run_bytes.argtypes = [P(_System), vp, i, i64, P(sz)]
+    L.heom_run_create.argtypes = [P(_System), vp, i, i64, P(d), P(d), P(d), vp, sz, vp, P(vp)]
+    L.heom_run_destroy.argtypes = [vp]
+    L.heom_propagate.argtypes = [vp, d, i64, i64]
+    L.heom_record_len.argtypes = [vp]
+    L.heom_observables.argtypes = [vp, P(d), i64, P(i64)]
+    L.heom_get_sigma0.argtypes = [vp, P(d), P(d)]
+    L.heom_get_ados.argtypes = [vp, i64, i64, P(d), P(d)]
+    L.heom_set_ados.argtypes = [vp, i64, i64, P(d), P(d)]
+    L.heom_rhs_eval.argtypes = [vp, i64, i64, P(d), P(d)]
+    L.heom_run_info.argtypes = [vp, P(i64), P(i), P(i), P(i64), P(d)]
+    L.heom_run_launches.argtypes = [vp]
+    L.heom_run_launches.restype = i64
+    for name in ABI_SYMBOLS:
+        if name not in ("heom_last_error", "heom_run_launches"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != HEOM_OK:
+        msg = load().heom_last_error()
+        raise HeomError(rc, msg.decode() if msg else "")
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Hierarchy:
+    """heom_build_hierarchy: multi-indices |n| <= depth over n_modes modes and their +/- links."""
+
+    def __init__(self, n_modes: int, depth: int):
+        L = load()
+        self._h = ctypes.c_void_p()
+        _check(L.heom_build_hierarchy(int(n_modes), int(depth), ctypes.byref(self._h)))
+        self.n_modes, self.depth = int(n_modes), int(depth)
+        n = ctypes.c_int64()
+        offs = (ctypes.c_int64 * (depth + 2))()
+        _check(L.heom_hier_info(self._h, ctypes.byref(n), offs))
+        self.n_ado = int(n.value)
+        self.level_offsets = np.array(list(offs), dtype=np.int64)
+
+    def export(self):
+        t = np.zeros((self.n_ado, self.n_modes), np.uint8)
+        p = np.zeros((self.n_ado, self.n_modes), np.int32)
+        m = np.zeros((self.n_ado, self.n_modes), np.int32)
+        _check(load().heom_hier_export(self._h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                       p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return t, p, m
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().heom_hier_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+
+class _SysArgs:
+    """Keeps the numpy arrays behind a heom_system alive."""
+
+    def __init__(self, system, terminator=True, rescale=True):
+        H = np.asarray(system.H)
+        self.H_re = np.ascontiguousarray(H.real, dtype=np.float64)
+        self.H_im = np.ascontiguousarray(H.imag, dtype=np.float64) if np.iscomplexobj(H) else None
+        self.bath_state = np.ascontiguousarray(system.bath_state, dtype=np.intc)
+        self.lam = np.ascontiguousarray(system.lambda_cm, dtype=np.float64)
+        self.tau = np.ascontiguousarray(system.tau_fs, dtype=np.float64)
+        self.T = np.ascontiguousarray(system.T_K, dtype=np.float64)
+        s = _System()
+        s.n_states = int(H.shape[0])
+        s.H_re = _dp(self.H_re)
+        s.H_im = _dp(self.H_im)
+        s.n_baths = len(self.bath_state)
+        s.bath_state = self.bath_state.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        s.lambda_cm = _dp(self.lam)
+        s.tau_fs = _dp(self.tau)
+        s.T_K = _dp(self.T)
+        s.n_matsubara = int(system.K)
+        s.terminator = int(bool(terminator))
+        s.rescale = int(bool(rescale))
+        self.s = s
+
+
+def run_bytes(system, hier: Hierarchy, precision="fp64", max_records=1, terminator=True, rescale=True) -> int:
+    sa = _SysArgs(system, terminator, rescale)
+    b = ctypes.c_size_t()
+    _check(load().heom_run_bytes(ctypes.byref(sa.s), hier._h, PRECISIONS[precision], int(max_records), ctypes.byref(b)))
+    return int(b.value)
+
+
+class Run:
+    """One propagation (heom_run_create) on a torch-allocated device workspace and torch stream."""
+
+    def __init__(self, system, rho0_re, rho0_im=None, precision="fp64", w=None, max_records=1024,
+                 terminator=True, rescale=True, hier: Hierarchy | None = None, stream=None, workspace=None):
+        import torch
+
+        L = load()
+        self.system = system
+        self.hier = hier if hier is not None else Hierarchy(system.n_modes, system.D)
+        self.precision = precision
+        self._sa = _SysArgs(system, terminator, rescale)
+        nbytes = ctypes.c_size_t()
+        _check(L.heom_run_bytes(ctypes.byref(self._sa.s), self.hier._h, PRECISIONS[precision], int(max_records),
+                                ctypes.byref(nbytes)))
+        self.workspace_bytes = int(nbytes.value)
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device="cuda")
+        self._ws = workspace
+        base = workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        avail = workspace.numel() - (aligned - base)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        r0 = np.ascontiguousarray(rho0_re, dtype=np.float64)
+        i0 = None if rho0_im is None else np.ascontiguousarray(rho0_im, dtype=np.float64)
+        wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        self._r = ctypes.c_void_p()
+        _check(L.heom_run_create(ctypes.byref(self._sa.s), self.hier._h, PRECISIONS[precision], int(max_records),
+                                 _dp(r0), _dp(i0), _dp(wv), ctypes.c_void_p(aligned), ctypes.c_size_t(avail),
+                                 ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(self._r)))
+        self.N = int(np.asarray(system.H).shape[0])
+        self.n_ado = self.hier.n_ado
+        self.record_len = int(L.heom_record_len(self._r))
+
+    def propagate(self, dt_fs: float, n_steps: int, obs_stride: int = 0):
+        _check(load().heom_propagate(self._r, float(dt_fs), int(n_steps), int(obs_stride)))
+
+    def observables(self, cap: int | None = None) -> np.ndarray:
+        cap = cap if cap is not None else 1 << 20
+        buf = np.zeros((cap, self.record_len))
+        written = ctypes.c_int64()
+        _check(load().heom_observables(self._r, _dp(buf), cap, ctypes.byref(written)))
+        return buf[: written.value].copy()
+
+    def sigma0(self) -> np.ndarray:
+        re = np.zeros((self.N, self.N))
+        im = np.zeros((self.N, self.N))
+        _check(load().heom_get_sigma0(self._r, _dp(re), _dp(im)))
+        return re + 1j * im
+
+    def get_ados(self, u0: int, count: int):
+        re = np.zeros((count, self.N, self.N))
+        im = np.zeros((count, self.N, self.N))
+        _check(load().heom_get_ados(self._r, int(u0), int(count), _dp(re), _dp(im)))
+        return re, im
+
+    def set_ados(self, u0: int, re: np.ndarray, im: np.ndarray):
+        re = np.ascontiguousarray(re, dtype=np.float64)
+        im = np.ascontiguousarray(im, dtype=np.float64)
+        _check(load().heom_set_ados(self._r, int(u0), int(re.shape[0]), _dp(re), _dp(im)))
+
+    def rhs_eval(self, u0: int, count: int):
+        re = np.zeros((count, self.N, self.N))
+        im = np.zeros((count, self.N, self.N))
+        _check(load().heom_rhs_eval(self._r, int(u0), int(count), _dp(re), _dp(im)))
+        return re, im
+
+    def info(self) -> dict:
+        n_ado, n, m, steps, t = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_double()
+        _check(load().heom_run_info(self._r, ctypes.byref(n_ado), ctypes.byref(n), ctypes.byref(m), ctypes.byref(steps),
+                                    ctypes.byref(t)))
+        return {"n_ado": n_ado.value, "n_states": n.value, "n_modes": m.value, "steps": steps.value, "t_fs": t.value}
+
+    def launches(self) -> int:
+        return int(load().heom_run_launches(self._r))
+
+    def close(self):
+        if getattr(self, "_r", None) is not None and self._r.value:
+            load().heom_run_destroy(self._r)
+            self._r = ctypes.c_void_p()
+
+    def __del__(self):
+        self.close()

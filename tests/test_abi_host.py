@@ -1,0 +1,97 @@
+"""Host-side checks of libheom that need no GPU: the library loads, exports every function that
+include/heom.h declares, builds the hierarchy bit-exactly like the oracle, and rejects bad
+arguments with the documented error codes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.oracle import hier_export
+from paper_1803_03498_gb300 import heom
+from paper_1803_03498_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1803_03498_gb300.build import build
+    build()
+    return heom.load()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "heom.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(heom_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(names) == sorted(heom.ABI_SYMBOLS)
+
+
+@pytest.mark.parametrize("M", range(1, 9))
+@pytest.mark.parametrize("D", range(0, 7))
+def test_hierarchy_bit_exact_small(lib, M, D):
+    h = heom.Hierarchy(M, D)
+    t, p, m = h.export()
+    to, po, mo = hier_export(M, D)
+    assert np.array_equal(t, to) and np.array_equal(p, po) and np.array_equal(m, mo)
+
+
+@pytest.mark.parametrize("M,D", [(2, 4), (14, 4), (28, 6)])
+def test_hierarchy_bit_exact_workloads(lib, M, D):
+    h = heom.Hierarchy(M, D)
+    t, p, m = h.export()
+    to, po, mo = hier_export(M, D)
+    assert t.tobytes() == to.tobytes()
+    assert p.tobytes() == po.tobytes()
+    assert m.tobytes() == mo.tobytes()
+    from math import comb
+    assert list(h.level_offsets) == [0] + [comb(M + L - 1, M) for L in range(1, D + 2)]
+
+
+def test_hierarchy_errors(lib):
+    for M, D, code in [(0, 2, heom.HEOM_E_ARG), (3, -1, heom.HEOM_E_ARG), (256, 1, heom.HEOM_E_ARG),
+                       (200, 10, heom.HEOM_E_OVERFLOW)]:
+        with pytest.raises(heom.HeomError) as ei:
+            heom.Hierarchy(M, D)
+        assert ei.value.code == code
+
+
+def test_run_bytes_and_argument_errors(lib):
+    p = wl.dimer()
+    h = heom.Hierarchy(p.system.n_modes, p.system.D)
+    b64 = heom.run_bytes(p.system, h, "fp64", 10)
+    b32 = heom.run_bytes(p.system, h, "fp32_mixed", 10)
+    assert b64 > 0 and b32 > 0
+    big = wl.lhcii_like().system
+    hb = heom.Hierarchy(big.n_modes, big.D)
+    n_ado, E = hb.n_ado, 14 * 14
+    assert heom.run_bytes(big, hb, "fp64", 1) >= 3 * n_ado * E * 16
+    assert heom.run_bytes(big, hb, "fp32_mixed", 1) >= 3 * n_ado * E * 8
+    assert heom.run_bytes(big, hb, "fp32_mixed", 1) < 3 * n_ado * E * 12
+    # mode count mismatch
+    with pytest.raises(heom.HeomError) as ei:
+        heom.run_bytes(p.system, heom.Hierarchy(3, 2), "fp64", 1)
+    assert ei.value.code == heom.HEOM_E_ARG
+    # unknown precision
+    sa = heom._SysArgs(p.system)
+    out = ctypes.c_size_t()
+    assert lib.heom_run_bytes(ctypes.byref(sa.s), h._h, 7, 1, ctypes.byref(out)) == heom.HEOM_E_ARG
+    # bath state out of range
+    bad = wl.System("bad", p.system.H, [0, 5], [35.0] * 2, [50.0] * 2, [300.0] * 2, K=0, D=4)
+    with pytest.raises(heom.HeomError):
+        heom.run_bytes(bad, h, "fp64", 1)
+    # too many states
+    H = np.eye(25)
+    bad = wl.System("big", H, [0], [35.0], [50.0], [300.0], K=0, D=1)
+    with pytest.raises(heom.HeomError):
+        heom.run_bytes(bad, heom.Hierarchy(1, 1), "fp64", 1)
+    assert "n_states" in lib.heom_last_error().decode()
