@@ -168,6 +168,23 @@ int heom_run_info(const heom_run *r, int64_t *n_ado, int *n_states, int *n_modes
 /* Kernel launches the library enqueued for this run since creation (all kinds). */
 int64_t heom_run_launches(const heom_run *r);
 
+/*
+ * Kernel timing of the dominant kernel (the stage kernel over the bulk of the hierarchy: every
+ * ADO for HEOM_FP64, levels >= 2 for HEOM_FP32_MIXED).  heom_run_set_timing(r, 1) starts recording
+ * a CUDA event pair around each such launch on the run's stream (and clears earlier records);
+ * 0 stops.  heom_run_kernel_time synchronises and returns the summed device time in ms, the number
+ * of timed launches, and the algorithmic bytes and flops of those launches:
+ *   bytes per ADO and launch = (tile reads + tile writes) * N^2 * complex size + M * 9 + 8
+ *     (a stage reads its input tile, reads y unless y is the input, writes one tile; the link
+ *      tables are 4 + 4 + 1 bytes per mode, the decay sum 8 bytes)
+ *   flops per ADO and launch = 8 N^3 (commutator with real H; 16 N^3 with complex H) + 8 N^2
+ *     (decay, terminator, RK4 combination) + 8 (N - 1) per valid up link + 8 (2N - 1) per valid
+ *     down link.
+ * Neighbour gathers count as algorithmically free.  At most 65536 launches are recorded.
+ */
+int heom_run_set_timing(heom_run *r, int enable);
+int heom_run_kernel_time(heom_run *r, double *ms, int64_t *launches, double *alg_bytes, double *alg_flops);
+
 #ifdef __cplusplus
 }
 #endif

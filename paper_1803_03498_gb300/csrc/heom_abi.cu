@@ -77,7 +77,15 @@ struct heom_run {
   int64_t steps_done = 0;
   double t_fs = 0;
   int64_t launches = 0;
-  size_t body_elem = 0;              // bytes per body complex element
+  // timing of the dominant kernel
+  bool timing = false;
+  bool pending = false;              // a begin event was recorded for the current launch
+  std::vector<cudaEvent_t> ev;       // pairs
+  double timed_bytes = 0, timed_flops = 0;
+  double bytes_stage_y = 0, bytes_stage_noy = 0, flops_stage = 0;  // per launch over the body range
+  ~heom_run() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 };
 
 extern "C" const char *heom_last_error(void) { return g_err.c_str(); }
@@ -378,6 +386,22 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     }
   }
 
+  {  // algorithmic bytes and flops of one launch of the dominant kernel (ADOs u >= u_split)
+    const double E = (double)n * n;
+    const double cs = (precision == HEOM_FP64) ? 16.0 : 8.0;
+    const double nb = (double)(h.n - r->u_split);
+    const double tab = nb * (M * 9.0 + 8.0);
+    r->bytes_stage_y = nb * 3.0 * E * cs + tab;
+    r->bytes_stage_noy = nb * 2.0 * E * cs + tab;
+    double up = 0, dn = 0;
+    for (int64_t u = r->u_split; u < h.n; ++u)
+      for (int l = 0; l < M; ++l) {
+        up += h.plus[(size_t)u * M + l] >= 0;
+        dn += h.minus[(size_t)u * M + l] >= 0;
+      }
+    r->flops_stage = nb * ((r->cplx_h ? 16.0 : 8.0) * n * E + 8.0 * E) + up * 8.0 * (n - 1) + dn * 8.0 * (2 * n - 1);
+  }
+
   char *base = reinterpret_cast<char *>(device_workspace);
   r->plusT = reinterpret_cast<int32_t *>(base + L.off_plus);
   r->minusT = reinterpret_cast<int32_t *>(base + L.off_minus);
@@ -458,17 +482,45 @@ static StageCommon common_for(const heom_run *r, StateView zin, StateView y, Sta
   return c;
 }
 
+static int timed_begin(heom_run *r) {
+  r->pending = false;
+  if (!r->timing || r->ev.size() >= 2 * 65536) return HEOM_OK;
+  cudaEvent_t a, b;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e != cudaSuccess) return cuda_fail("timing event", e);
+  r->ev.push_back(a);
+  r->ev.push_back(b);
+  e = cudaEventRecord(a, r->stream);
+  if (e != cudaSuccess) return cuda_fail("timing event record", e);
+  r->pending = true;
+  return HEOM_OK;
+}
+
+static int timed_end(heom_run *r, double bytes) {
+  if (!r->pending) return HEOM_OK;
+  r->pending = false;
+  cudaError_t e = cudaEventRecord(r->ev.back(), r->stream);
+  if (e != cudaSuccess) return cuda_fail("timing event record", e);
+  r->timed_bytes += bytes;
+  r->timed_flops += r->flops_stage;
+  return HEOM_OK;
+}
+
 static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, double ch) {
   StageCommon c = common_for(r, zin, y, out);
   const double *Hi = r->cplx_h ? r->Hi.data() : nullptr;
   int rc;
+  const bool same_y = (y.head == zin.head && y.body == zin.body);
+  const bool no_y = (y.head == nullptr && y.body == nullptr);
   if (r->precision == HEOM_FP64) {
     c.u_begin = 0;
     c.u_end = (int)r->n_ado;
+    if ((rc = timed_begin(r))) return rc;
     rc = launch_stage(0, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
     if (rc) return HEOM_E_CUDA;
     ++r->launches;
-    return HEOM_OK;
+    return timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y);
   }
   // mixed: FP64 head (levels 0, 1) and FP32 body
   c.u_begin = 0;
@@ -479,10 +531,41 @@ static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, dou
   c.u_begin = r->u_split;
   c.u_end = (int)r->n_ado;
   if (c.u_end > c.u_begin) {
+    if ((rc = timed_begin(r))) return rc;
     rc = launch_stage(1, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
     if (rc) return HEOM_E_CUDA;
     ++r->launches;
+    return timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y);
   }
+  return HEOM_OK;
+}
+
+extern "C" int heom_run_set_timing(heom_run *r, int enable) {
+  if (!r) { set_error("heom_run_set_timing: NULL run"); return HEOM_E_ARG; }
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail("heom_run_set_timing: stream", e);
+  for (cudaEvent_t ev : r->ev) cudaEventDestroy(ev);
+  r->ev.clear();
+  r->timed_bytes = r->timed_flops = 0;
+  r->timing = enable != 0;
+  return HEOM_OK;
+}
+
+extern "C" int heom_run_kernel_time(heom_run *r, double *ms, int64_t *launches, double *alg_bytes, double *alg_flops) {
+  if (!r) { set_error("heom_run_kernel_time: NULL run"); return HEOM_E_ARG; }
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail("heom_run_kernel_time: stream", e);
+  double tot = 0;
+  for (size_t i = 0; i + 1 < r->ev.size(); i += 2) {
+    float t = 0;
+    e = cudaEventElapsedTime(&t, r->ev[i], r->ev[i + 1]);
+    if (e != cudaSuccess) return cuda_fail("heom_run_kernel_time: elapsed", e);
+    tot += t;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = (int64_t)(r->ev.size() / 2);
+  if (alg_bytes) *alg_bytes = r->timed_bytes;
+  if (alg_flops) *alg_flops = r->timed_flops;
   return HEOM_OK;
 }
 

@@ -24,7 +24,7 @@ ABI_SYMBOLS = [
     "heom_last_error", "heom_build_hierarchy", "heom_hier_destroy", "heom_hier_info", "heom_hier_export",
     "heom_run_bytes", "heom_run_create", "heom_run_destroy", "heom_propagate", "heom_record_len",
     "heom_observables", "heom_get_sigma0", "heom_get_ados", "heom_set_ados", "heom_rhs_eval", "heom_run_info",
-    "heom_run_launches",
+    "heom_run_launches", "heom_run_set_timing", "heom_run_kernel_time",
 ]
 
 
@@ -82,6 +82,8 @@ def load():
     L.heom_run_info.argtypes = [vp, P(i64), P(i), P(i), P(i64), P(d)]
     L.heom_run_launches.argtypes = [vp]
     L.heom_run_launches.restype = i64
+    L.heom_run_set_timing.argtypes = [vp, i]
+    L.heom_run_kernel_time.argtypes = [vp, P(d), P(i64), P(d), P(d)]
     for name in ABI_SYMBOLS:
         if name not in ("heom_last_error", "heom_run_launches"):
             getattr(L, name).restype = ctypes.c_int
@@ -236,6 +238,14 @@ class Run:
 
     def launches(self) -> int:
         return int(load().heom_run_launches(self._r))
+
+    def set_timing(self, enable: bool):
+        _check(load().heom_run_set_timing(self._r, int(bool(enable))))
+
+    def kernel_time(self) -> dict:
+        ms, n, b, f = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(load().heom_run_kernel_time(self._r, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b), ctypes.byref(f)))
+        return {"ms": ms.value, "launches": n.value, "alg_bytes": b.value, "alg_flops": f.value}
 
     def close(self):
         if getattr(self, "_r", None) is not None and self._r.value:
