@@ -19,17 +19,13 @@ void set_error(const std::string &msg) { g_err = msg; }
 int launch_stage(int precision, const StageCommon &c, double ch, const double *term, const double *H,
                  const double *Hi, cudaStream_t st, int sm_count) {
   if (c.u_end <= c.u_begin) return 0;
-  int rc;
-  if (precision == 0) {
-    rc = launch_stage_fp64_lo(c, ch, term, H, Hi, st, sm_count);
-    if (rc == 1) rc = launch_stage_fp64_hi(c, ch, term, H, Hi, st, sm_count);
-  } else if (precision == 1) {
-    rc = launch_stage_fp32_lo(c, ch, term, H, Hi, st, sm_count);
-    if (rc == 1) rc = launch_stage_fp32_hi(c, ch, term, H, Hi, st, sm_count);
-  } else {
-    rc = launch_stage_head_lo(c, ch, term, H, Hi, st, sm_count);
-    if (rc == 1) rc = launch_stage_head_hi(c, ch, term, H, Hi, st, sm_count);
-  }
+  static int (*const fns[3][4])(const StageCommon &, double, const double *, const double *, const double *,
+                                 cudaStream_t, int) = {
+      {launch_stage_fp64_a, launch_stage_fp64_b, launch_stage_fp64_c, launch_stage_fp64_d},
+      {launch_stage_fp32_a, launch_stage_fp32_b, launch_stage_fp32_c, launch_stage_fp32_d},
+      {launch_stage_head_a, launch_stage_head_b, launch_stage_head_c, launch_stage_head_d}};
+  int rc = 1;
+  for (int g = 0; g < 4 && rc == 1; ++g) rc = fns[precision][g](c, ch, term, H, Hi, st, sm_count);
   if (rc == 1) {
     set_error("stage kernel: n_states not compiled");
     return -1;
@@ -54,7 +50,7 @@ struct heom_run {
   int n = 0, M = 0, D = 0, K = 0, B = 0;
   int64_t n_ado = 0;
   int u_split = 0;                   // ADOs stored in FP64 in the head region
-  int64_t head_pitch = 0, body_pitch = 0, u_pitch = 0;
+  int E = 0, Ep = 0, Mp = 0;         // tile size, body tile pitch, padded mode count
   cudaStream_t stream = nullptr;
   int sm_count = 0;
   // host copies of the per-run constants (rad/fs)
@@ -64,8 +60,8 @@ struct heom_run {
   double max_rate = 0;               // D * max gamma
   // device
   StateView y{}, zA{}, zB{};
-  int32_t *plusT = nullptr, *minusT = nullptr;
-  uint8_t *tupT = nullptr;
+  int32_t *plusA = nullptr, *minusA = nullptr;
+  uint8_t *tupA = nullptr;
   double *gsum = nullptr, *sp_tab = nullptr, *sm_tab = nullptr;
   ModeDev *modes = nullptr;
   int *state_mode_off = nullptr;
@@ -173,20 +169,18 @@ int check_system(const heom_system *s, const heom_hier *h, int precision) {
   return HEOM_OK;
 }
 
-Layout make_layout(int n, int M, int D, int64_t n_ado, int u_split, int precision, int64_t max_records,
-                   int64_t *head_pitch, int64_t *body_pitch, int64_t *u_pitch) {
+Layout make_layout(int n, int M, int D, int64_t n_ado, int u_split, int precision, int64_t max_records, int *Ep,
+                   int *Mp) {
   Layout L{};
   const int64_t E = (int64_t)n * n;
-  *u_pitch = (n_ado + 63) / 64 * 64;
-  *head_pitch = (u_split + 63) / 64 * 64;
-  const int64_t nb = n_ado - u_split;
-  *body_pitch = (nb + 63) / 64 * 64;
   const size_t be = (precision == HEOM_FP64) ? sizeof(double2) : sizeof(float2);
+  *Ep = (int)((be == sizeof(float2) && (E & 1)) ? E + 1 : E);
+  *Mp = (M + 15) / 16 * 16;
   size_t o = 0;
-  L.off_plus = o; o = al(o + (size_t)M * *u_pitch * sizeof(int32_t));
-  L.off_minus = o; o = al(o + (size_t)M * *u_pitch * sizeof(int32_t));
-  L.off_tup = o; o = al(o + (size_t)M * *u_pitch);
-  L.off_gsum = o; o = al(o + (size_t)*u_pitch * sizeof(double));
+  L.off_plus = o; o = al(o + (size_t)n_ado * *Mp * sizeof(int32_t));
+  L.off_minus = o; o = al(o + (size_t)n_ado * *Mp * sizeof(int32_t));
+  L.off_tup = o; o = al(o + (size_t)n_ado * *Mp);
+  L.off_gsum = o; o = al(o + (size_t)n_ado * sizeof(double));
   L.off_sp = o; o = al(o + (size_t)M * (D + 1) * sizeof(double));
   L.off_sm = o; o = al(o + (size_t)M * (D + 1) * sizeof(double));
   L.off_modes = o; o = al(o + (size_t)M * sizeof(ModeDev));
@@ -194,8 +188,8 @@ Layout make_layout(int n, int M, int D, int64_t n_ado, int u_split, int precisio
   L.off_rec = o; o = al(o + (size_t)std::max<int64_t>(max_records, 1) * (n + 5) * sizeof(double));
   L.off_w = o; o = al(o + (size_t)n * sizeof(double));
   L.off_cnt = o; o = al(o + sizeof(int64_t));
-  L.head_bytes = al((size_t)E * *head_pitch * sizeof(double2));
-  L.body_bytes = al((size_t)E * *body_pitch * be);
+  L.head_bytes = al((size_t)u_split * E * sizeof(double2));
+  L.body_bytes = al((size_t)(n_ado - u_split) * *Ep * be);
   for (int c = 0; c < 3; ++c) {
     L.off_state[c] = o;
     o = al(o + L.head_bytes + L.body_bytes);
@@ -216,20 +210,20 @@ extern "C" int heom_run_bytes(const heom_system *sys, const heom_hier *h, int pr
   int rc = check_system(sys, h, precision);
   if (rc) return rc;
   if (!bytes || max_records < 0) { set_error("heom_run_bytes: bad output pointer or max_records"); return HEOM_E_ARG; }
-  int64_t hp, bp, up;
+  int Ep, Mp;
   const int u_split = (precision == HEOM_FP64) ? 0 : (int)std::min<int64_t>(h->h.n, h->h.level_off[std::min(2, h->h.D + 1)]);
-  Layout L = make_layout(sys->n_states, h->h.M, h->h.D, h->h.n, u_split, precision, max_records, &hp, &bp, &up);
+  Layout L = make_layout(sys->n_states, h->h.M, h->h.D, h->h.n, u_split, precision, max_records, &Ep, &Mp);
   *bytes = L.total;
   return HEOM_OK;
 }
 
 namespace heom {
-__global__ void record_kernel(StateView y, int64_t hp, int64_t bp, int u_split, int n, const double *w,
-                              double *records, int64_t *rec_count, int64_t max_records, int is_fp64_body);
-__global__ void scatter_kernel(StateView dst, int64_t hp, int64_t bp, int u_split, int body_fp32, int n, int64_t u0,
-                               int64_t count, const double *re, const double *im);
-__global__ void gather_kernel(StateView src, int64_t hp, int64_t bp, int u_split, int body_fp32, int n, int64_t u0,
-                              int64_t count, double *re, double *im);
+__global__ void record_kernel(StateView y, int u_split, int body_fp32, int n, const double *w, double *records,
+                              int64_t *rec_count, int64_t max_records);
+__global__ void scatter_kernel(StateView dst, int Ep, int u_split, int body_fp32, int n, int64_t u0, int64_t count,
+                               const double *re, const double *im);
+__global__ void gather_kernel(StateView src, int Ep, int u_split, int body_fp32, int n, int64_t u0, int64_t count,
+                              double *re, double *im);
 }  // namespace heom
 
 static StateView view_at(char *base, const Layout &L, int c) {
@@ -244,8 +238,8 @@ static int enqueue_record(heom_run *r) {
     set_error("observable record buffer full (max_records)");
     return HEOM_E_NOMEM;
   }
-  record_kernel<<<1, 32, 0, r->stream>>>(r->y, r->head_pitch, r->body_pitch, r->u_split, r->n, r->w_dev, r->records,
-                                         r->rec_count, r->max_records, r->precision == HEOM_FP64);
+  record_kernel<<<1, 32, 0, r->stream>>>(r->y, r->u_split, r->precision != HEOM_FP64, r->n, r->w_dev, r->records,
+                                         r->rec_count, r->max_records);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail("record kernel launch", e);
   ++r->records_host;
@@ -275,7 +269,8 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   r->u_split = (precision == HEOM_FP64) ? 0 : (int)std::min<int64_t>(h.n, h.level_off[std::min(2, D + 1)]);
   r->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   r->max_records = max_records;
-  Layout L = make_layout(n, M, D, h.n, r->u_split, precision, max_records, &r->head_pitch, &r->body_pitch, &r->u_pitch);
+  Layout L = make_layout(n, M, D, h.n, r->u_split, precision, max_records, &r->Ep, &r->Mp);
+  r->E = n * n;
   if (workspace_bytes < L.total) {
     delete r;
     set_error("workspace too small: need " + std::to_string(L.total) + " bytes");
@@ -361,14 +356,15 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     }
   }
 
-  // ---- tables, transposed to [q][u] so consecutive ADOs are contiguous
-  std::vector<int32_t> plusT, minusT;
-  std::vector<uint8_t> tupT;
-  std::vector<double> gs(r->u_pitch, 0.0);
+  // ---- tables, one row of Mp entries per ADO, modes in state order
+  const int Mp = r->Mp;
+  std::vector<int32_t> plusA, minusA;
+  std::vector<uint8_t> tupA;
+  std::vector<double> gs(h.n, 0.0);
   try {
-    plusT.assign((size_t)M * r->u_pitch, -1);
-    minusT.assign((size_t)M * r->u_pitch, -1);
-    tupT.assign((size_t)M * r->u_pitch, 0);
+    plusA.assign((size_t)h.n * Mp, -1);
+    minusA.assign((size_t)h.n * Mp, -1);
+    tupA.assign((size_t)h.n * Mp, 0);
   } catch (...) {
     delete r;
     set_error("host allocation failed (tables)");
@@ -380,9 +376,9 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     gs[u] = g;
     for (int q = 0; q < M; ++q) {
       const int l = perm[q];
-      plusT[(size_t)q * r->u_pitch + u] = h.plus[(size_t)u * M + l];
-      minusT[(size_t)q * r->u_pitch + u] = h.minus[(size_t)u * M + l];
-      tupT[(size_t)q * r->u_pitch + u] = h.tuples[(size_t)u * M + l];
+      plusA[(size_t)u * Mp + q] = h.plus[(size_t)u * M + l];
+      minusA[(size_t)u * Mp + q] = h.minus[(size_t)u * M + l];
+      tupA[(size_t)u * Mp + q] = h.tuples[(size_t)u * M + l];
     }
   }
 
@@ -390,7 +386,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     const double E = (double)n * n;
     const double cs = (precision == HEOM_FP64) ? 16.0 : 8.0;
     const double nb = (double)(h.n - r->u_split);
-    const double tab = nb * (M * 9.0 + 8.0);
+    const double tab = nb * (r->Mp * 9.0 + 8.0);
     r->bytes_stage_y = nb * 3.0 * E * cs + tab;
     r->bytes_stage_noy = nb * 2.0 * E * cs + tab;
     double up = 0, dn = 0;
@@ -403,9 +399,9 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   }
 
   char *base = reinterpret_cast<char *>(device_workspace);
-  r->plusT = reinterpret_cast<int32_t *>(base + L.off_plus);
-  r->minusT = reinterpret_cast<int32_t *>(base + L.off_minus);
-  r->tupT = reinterpret_cast<uint8_t *>(base + L.off_tup);
+  r->plusA = reinterpret_cast<int32_t *>(base + L.off_plus);
+  r->minusA = reinterpret_cast<int32_t *>(base + L.off_minus);
+  r->tupA = reinterpret_cast<uint8_t *>(base + L.off_tup);
   r->gsum = reinterpret_cast<double *>(base + L.off_gsum);
   r->sp_tab = reinterpret_cast<double *>(base + L.off_sp);
   r->sm_tab = reinterpret_cast<double *>(base + L.off_sm);
@@ -421,9 +417,9 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   std::vector<double> w(n, 0.0);
   if (dip_w) for (int i = 0; i < n; ++i) w[i] = dip_w[i];
   cudaStream_t st = r->stream;
-  ce = cudaMemcpyAsync(r->plusT, plusT.data(), plusT.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->minusT, minusT.data(), minusT.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->tupT, tupT.data(), tupT.size(), cudaMemcpyHostToDevice, st);
+  ce = cudaMemcpyAsync(r->plusA, plusA.data(), plusA.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->minusA, minusA.data(), minusA.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->tupA, tupA.data(), tupA.size(), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->gsum, gs.data(), gs.size() * sizeof(double), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->sp_tab, sp.data(), sp.size() * sizeof(double), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->sm_tab, sm.data(), sm.size() * sizeof(double), cudaMemcpyHostToDevice, st);
@@ -462,17 +458,17 @@ static StageCommon common_for(const heom_run *r, StateView zin, StateView y, Sta
   c.zin = zin;
   c.y = y;
   c.out = out;
-  c.plusT = r->plusT;
-  c.minusT = r->minusT;
-  c.tupT = r->tupT;
+  c.plusA = r->plusA;
+  c.minusA = r->minusA;
+  c.tupA = r->tupA;
   c.gsum = r->gsum;
   c.modes = r->modes;
   c.state_mode_off = r->state_mode_off;
   c.sp_tab = r->sp_tab;
   c.sm_tab = r->sm_tab;
-  c.head_pitch = r->head_pitch;
-  c.body_pitch = r->body_pitch;
-  c.u_pitch = r->u_pitch;
+  c.E = r->E;
+  c.Ep = r->Ep;
+  c.Mp = r->Mp;
   c.u_split = r->u_split;
   c.n_ado = (int)r->n_ado;
   c.n = r->n;
@@ -631,8 +627,8 @@ extern "C" int heom_observables(heom_run *r, double *out, int64_t cap_records, i
 
 static int64_t staging_ados(const heom_run *r) {
   // zB holds (head + body) bytes; every staged ADO needs 2 * N^2 doubles
-  const size_t bytes = (size_t)(r->n * r->n) * (r->head_pitch * sizeof(double2) +
-                                                r->body_pitch * (r->precision == HEOM_FP64 ? 16 : 8));
+  const size_t bytes = (size_t)r->u_split * r->E * sizeof(double2) +
+                       (size_t)(r->n_ado - r->u_split) * r->Ep * (r->precision == HEOM_FP64 ? 16 : 8);
   return std::max<int64_t>(1, (int64_t)(bytes / (2 * sizeof(double) * r->n * r->n)));
 }
 
@@ -653,8 +649,8 @@ static int io_range(heom_run *r, StateView state, int64_t u0, int64_t count, dou
       if (e == cudaSuccess) e = cudaMemcpyAsync(st_im, im + c0 * E, cc * E * sizeof(double), cudaMemcpyHostToDevice, r->stream);
       if (e != cudaSuccess) return cuda_fail("state upload", e);
       const int blocks = (int)std::min<int64_t>((cc * E + 255) / 256, 65535);
-      scatter_kernel<<<blocks, 256, 0, r->stream>>>(state, r->head_pitch, r->body_pitch, r->u_split,
-                                                   r->precision != HEOM_FP64, r->n, u0 + c0, cc, st_re, st_im);
+      scatter_kernel<<<blocks, 256, 0, r->stream>>>(state, r->Ep, r->u_split, r->precision != HEOM_FP64, r->n, u0 + c0,
+                                                   cc, st_re, st_im);
       ++r->launches;
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail("scatter kernel", e);
@@ -662,8 +658,8 @@ static int io_range(heom_run *r, StateView state, int64_t u0, int64_t count, dou
       if (e != cudaSuccess) return cuda_fail("state upload sync", e);
     } else {
       const int blocks = (int)std::min<int64_t>((cc * E + 255) / 256, 65535);
-      gather_kernel<<<blocks, 256, 0, r->stream>>>(state, r->head_pitch, r->body_pitch, r->u_split,
-                                                  r->precision != HEOM_FP64, r->n, u0 + c0, cc, st_re, st_im);
+      gather_kernel<<<blocks, 256, 0, r->stream>>>(state, r->Ep, r->u_split, r->precision != HEOM_FP64, r->n, u0 + c0,
+                                                  cc, st_re, st_im);
       ++r->launches;
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail("gather kernel", e);
@@ -718,35 +714,36 @@ extern "C" int64_t heom_run_launches(const heom_run *r) { return r ? r->launches
 
 namespace heom {
 
-__device__ __forceinline__ double2 ld_any(const StateView &s, int64_t hp, int64_t bp, int u_split, int body_fp32,
-                                          int64_t e, int64_t v) {
-  if (v < u_split) return s.head[e * hp + v];
+__device__ __forceinline__ double2 ld_any(const StateView &s, int E, int Ep, int u_split, int body_fp32, int64_t v,
+                                          int64_t e) {
+  if (v < u_split) return s.head[v * E + e];
   if (body_fp32) {
-    float2 f = reinterpret_cast<const float2 *>(s.body)[e * bp + (v - u_split)];
+    const float2 f = reinterpret_cast<const float2 *>(s.body)[(v - u_split) * Ep + e];
     return make_double2(f.x, f.y);
   }
-  return reinterpret_cast<const double2 *>(s.body)[e * bp + (v - u_split)];
+  return reinterpret_cast<const double2 *>(s.body)[(v - u_split) * Ep + e];
 }
 
 // One observable record of sigma_0 (FP64): populations, trace, dipole correlation, Hermiticity.
-__global__ void record_kernel(StateView y, int64_t hp, int64_t bp, int u_split, int n, const double *w,
-                              double *records, int64_t *rec_count, int64_t max_records, int is_fp64_body) {
+__global__ void record_kernel(StateView y, int u_split, int body_fp32, int n, const double *w, double *records,
+                              int64_t *rec_count, int64_t max_records) {
   if (threadIdx.x != 0) return;
   const int64_t idx = *rec_count;
   if (idx >= max_records) return;
+  const int E = n * n;
   double *rec = records + idx * (n + 5);
   double tr = 0, ti = 0, cr = 0, ci = 0, herm = 0;
   for (int a = 0; a < n; ++a) {
-    const double2 d = ld_any(y, hp, bp, u_split, !is_fp64_body, (int64_t)a * n + a, 0);
+    const double2 d = ld_any(y, E, E, u_split, body_fp32, 0, (int64_t)a * n + a);
     rec[a] = d.x;
     tr += d.x;
     ti += d.y;
-    const double2 c0 = ld_any(y, hp, bp, u_split, !is_fp64_body, (int64_t)a * n, 0);
+    const double2 c0 = ld_any(y, E, E, u_split, body_fp32, 0, (int64_t)a * n);
     cr += w[a] * c0.x;
     ci += w[a] * c0.y;
     for (int b = 0; b < n; ++b) {
-      const double2 x = ld_any(y, hp, bp, u_split, !is_fp64_body, (int64_t)a * n + b, 0);
-      const double2 z = ld_any(y, hp, bp, u_split, !is_fp64_body, (int64_t)b * n + a, 0);
+      const double2 x = ld_any(y, E, E, u_split, body_fp32, 0, (int64_t)a * n + b);
+      const double2 z = ld_any(y, E, E, u_split, body_fp32, 0, (int64_t)b * n + a);
       herm = fmax(herm, hypot(x.x - z.x, x.y + z.y));
     }
   }
@@ -758,28 +755,28 @@ __global__ void record_kernel(StateView y, int64_t hp, int64_t bp, int u_split, 
   *rec_count = idx + 1;
 }
 
-__global__ void scatter_kernel(StateView dst, int64_t hp, int64_t bp, int u_split, int body_fp32, int n, int64_t u0,
-                               int64_t count, const double *re, const double *im) {
+__global__ void scatter_kernel(StateView dst, int Ep, int u_split, int body_fp32, int n, int64_t u0, int64_t count,
+                               const double *re, const double *im) {
   const int64_t E = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count * E; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = t / E, e = t - c * E;
     const int64_t v = u0 + c;
     if (v < u_split) {
-      dst.head[e * hp + v] = make_double2(re[t], im[t]);
+      dst.head[v * E + e] = make_double2(re[t], im[t]);
     } else if (body_fp32) {
-      reinterpret_cast<float2 *>(dst.body)[e * bp + (v - u_split)] = make_float2((float)re[t], (float)im[t]);
+      reinterpret_cast<float2 *>(dst.body)[(v - u_split) * Ep + e] = make_float2((float)re[t], (float)im[t]);
     } else {
-      reinterpret_cast<double2 *>(dst.body)[e * bp + (v - u_split)] = make_double2(re[t], im[t]);
+      reinterpret_cast<double2 *>(dst.body)[(v - u_split) * Ep + e] = make_double2(re[t], im[t]);
     }
   }
 }
 
-__global__ void gather_kernel(StateView src, int64_t hp, int64_t bp, int u_split, int body_fp32, int n, int64_t u0,
-                              int64_t count, double *re, double *im) {
+__global__ void gather_kernel(StateView src, int Ep, int u_split, int body_fp32, int n, int64_t u0, int64_t count,
+                              double *re, double *im) {
   const int64_t E = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count * E; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = t / E, e = t - c * E;
-    const double2 d = ld_any(src, hp, bp, u_split, body_fp32, e, u0 + c);
+    const double2 d = ld_any(src, (int)E, Ep, u_split, body_fp32, u0 + c, e);
     re[t] = d.x;
     im[t] = d.y;
   }

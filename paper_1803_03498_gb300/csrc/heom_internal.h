@@ -24,8 +24,9 @@ struct ModeDev {
 };
 
 // Hierarchy state storage of one RK4 copy: ADOs u < u_split ("head") as FP64 complex, ADOs
-// u >= u_split ("body") as complex of the run's storage type; both element-major, so element e of
-// ADOs u, u+1, ... is contiguous: head[e * head_pitch + u], body[e * body_pitch + (u - u_split)].
+// u >= u_split ("body") as complex of the run's storage type.  Every ADO's N x N tile is contiguous
+// and row-major: head[u * E + e], body[(u - u_split) * Ep + e] with E = N^2 and Ep = E rounded up so
+// that a body tile is a multiple of 16 bytes.
 struct StateView {
   double2 *head;
   void *body;
@@ -36,15 +37,15 @@ struct StageCommon {
   StateView zin;        // state the RHS is evaluated on (own tile and neighbour gathers)
   StateView y;          // Horner base y (head == nullptr && body == nullptr: none)
   StateView out;        // result y + ch * L zin (or ch * L zin)
-  const int32_t *plusT; // [M][u_pitch]
-  const int32_t *minusT;
-  const uint8_t *tupT;  // [M][u_pitch]
-  const double *gsum;   // [u_pitch] sum_l n_l gamma_l
+  const int32_t *plusA; // [n_ado][Mp], modes in state order, -1 = no link
+  const int32_t *minusA;
+  const uint8_t *tupA;  // [n_ado][Mp] n_l
+  const double *gsum;   // [n_ado] sum_l n_l gamma_l
   const ModeDev *modes; // [M], ordered by state
   const int *state_mode_off;  // [n + 1] modes of state s: [off[s], off[s+1])
   const double *sp_tab;       // [M][D + 1] up factor  s+_l(n_l)
   const double *sm_tab;       // [M][D + 1] down factor s-_l(n_l)
-  int64_t head_pitch, body_pitch, u_pitch;
+  int E, Ep, Mp;        // N^2, body tile pitch, padded mode count (multiple of 16)
   int u_split, n_ado;
   int u_begin, u_end;   // ADO range of this launch
   int n, M, D;
@@ -65,12 +66,18 @@ struct StageArgs {
 #define HEOM_DECLARE_LAUNCH(NAME)                                                                      \
   int NAME(const StageCommon &c, double ch, const double *term, const double *H, const double *Hi, \
            cudaStream_t st, int sm_count);
-HEOM_DECLARE_LAUNCH(launch_stage_fp64_lo)
-HEOM_DECLARE_LAUNCH(launch_stage_fp64_hi)
-HEOM_DECLARE_LAUNCH(launch_stage_fp32_lo)
-HEOM_DECLARE_LAUNCH(launch_stage_fp32_hi)
-HEOM_DECLARE_LAUNCH(launch_stage_head_lo)
-HEOM_DECLARE_LAUNCH(launch_stage_head_hi)
+HEOM_DECLARE_LAUNCH(launch_stage_fp64_a)
+HEOM_DECLARE_LAUNCH(launch_stage_fp64_b)
+HEOM_DECLARE_LAUNCH(launch_stage_fp64_c)
+HEOM_DECLARE_LAUNCH(launch_stage_fp64_d)
+HEOM_DECLARE_LAUNCH(launch_stage_fp32_a)
+HEOM_DECLARE_LAUNCH(launch_stage_fp32_b)
+HEOM_DECLARE_LAUNCH(launch_stage_fp32_c)
+HEOM_DECLARE_LAUNCH(launch_stage_fp32_d)
+HEOM_DECLARE_LAUNCH(launch_stage_head_a)
+HEOM_DECLARE_LAUNCH(launch_stage_head_b)
+HEOM_DECLARE_LAUNCH(launch_stage_head_c)
+HEOM_DECLARE_LAUNCH(launch_stage_head_d)
 #undef HEOM_DECLARE_LAUNCH
 
 // precision: 0 = FP64 (compute and storage double), 1 = mixed body (float, float), 2 = mixed head

@@ -1,0 +1,20 @@
+// Instantiations of the stage kernel: compute double, storage double, n_states 13..18.
+#include "stage_kernel.cuh"
+
+namespace heom {
+
+int launch_stage_fp64_c(const StageCommon &c, double ch, const double *term, const double *H, const double *Hi,
+                       cudaStream_t st, int sm_count) {
+  switch (c.n) {
+    case 13: return launch_n<13, double, double>(c, ch, term, H, Hi, st, sm_count);
+    case 14: return launch_n<14, double, double>(c, ch, term, H, Hi, st, sm_count);
+    case 15: return launch_n<15, double, double>(c, ch, term, H, Hi, st, sm_count);
+    case 16: return launch_n<16, double, double>(c, ch, term, H, Hi, st, sm_count);
+    case 17: return launch_n<17, double, double>(c, ch, term, H, Hi, st, sm_count);
+    case 18: return launch_n<18, double, double>(c, ch, term, H, Hi, st, sm_count);
+    default:
+      return 1;  // not in this translation unit
+  }
+}
+
+}  // namespace heom
