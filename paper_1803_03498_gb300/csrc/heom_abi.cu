@@ -50,7 +50,7 @@ struct heom_run {
   int n = 0, M = 0, D = 0, K = 0, B = 0;
   int64_t n_ado = 0;
   int u_split = 0;                   // ADOs stored in FP64 in the head region
-  int E = 0, Ep = 0, Mp = 0;         // tile size, body tile pitch, padded mode count
+  int E = 0, Ep = 0;                 // tile size, body tile pitch
   cudaStream_t stream = nullptr;
   int sm_count = 0;
   // host copies of the per-run constants (rad/fs)
@@ -60,11 +60,11 @@ struct heom_run {
   double max_rate = 0;               // D * max gamma
   // device
   StateView y{}, zA{}, zB{};
-  int32_t *plusA = nullptr, *minusA = nullptr;
-  uint8_t *tupA = nullptr;
-  double *gsum = nullptr, *sp_tab = nullptr, *sm_tab = nullptr;
-  ModeDev *modes = nullptr;
-  int *state_mode_off = nullptr;
+  int64_t *link_off = nullptr;       // [n_ado + 1]
+  void *recs_head = nullptr;         // LinkRec<double>, ADOs u < u_split
+  void *recs_body = nullptr;         // LinkRec<float or double>, ADOs u >= u_split
+  int64_t rec_split = 0;             // link_off[u_split]
+  double *gsum = nullptr;
   double *records = nullptr;         // [max_records][n + 5]
   double *w_dev = nullptr;           // [n] dipole weights (zeros if none)
   int64_t *rec_count = nullptr;      // device counter of records written
@@ -129,7 +129,7 @@ extern "C" int heom_hier_export(const heom_hier *h, uint8_t *tuples, int32_t *pl
 namespace {
 
 struct Layout {
-  size_t off_plus, off_minus, off_tup, off_gsum, off_sp, off_sm, off_modes, off_smo, off_rec, off_w, off_cnt;
+  size_t off_loff, off_rh, off_rb, off_gsum, off_rec, off_w, off_cnt;
   size_t off_state[3];
   size_t head_bytes, body_bytes;
   size_t total;
@@ -169,22 +169,32 @@ int check_system(const heom_system *s, const heom_hier *h, int precision) {
   return HEOM_OK;
 }
 
-Layout make_layout(int n, int M, int D, int64_t n_ado, int u_split, int precision, int64_t max_records, int *Ep,
-                   int *Mp) {
+// Valid links (up and down) of the ADOs [u_lo, u_hi).
+int64_t count_links(const Hierarchy &h, int64_t u_lo, int64_t u_hi) {
+  int64_t k = 0;
+  for (int64_t u = u_lo; u < u_hi; ++u)
+    for (int l = 0; l < h.M; ++l) k += (h.plus[(size_t)u * h.M + l] >= 0) + (h.minus[(size_t)u * h.M + l] >= 0);
+  return k;
+}
+
+int split_of(const Hierarchy &h, int precision) {
+  return (precision == HEOM_FP64) ? 0 : (int)std::min<int64_t>(h.n, h.level_off[std::min(2, h.D + 1)]);
+}
+
+Layout make_layout(int n, const Hierarchy &h, int u_split, int precision, int64_t max_records, int *Ep) {
   Layout L{};
   const int64_t E = (int64_t)n * n;
+  const int64_t n_ado = h.n;
   const size_t be = (precision == HEOM_FP64) ? sizeof(double2) : sizeof(float2);
+  const size_t rb = (precision == HEOM_FP64) ? sizeof(LinkRec<double>) : sizeof(LinkRec<float>);
   *Ep = (int)((be == sizeof(float2) && (E & 1)) ? E + 1 : E);
-  *Mp = (M + 15) / 16 * 16;
+  const int64_t lh = count_links(h, 0, u_split);
+  const int64_t lb = h.n_links - lh;
   size_t o = 0;
-  L.off_plus = o; o = al(o + (size_t)n_ado * *Mp * sizeof(int32_t));
-  L.off_minus = o; o = al(o + (size_t)n_ado * *Mp * sizeof(int32_t));
-  L.off_tup = o; o = al(o + (size_t)n_ado * *Mp);
+  L.off_loff = o; o = al(o + (size_t)(n_ado + 1) * sizeof(int64_t));
+  L.off_rh = o; o = al(o + (size_t)lh * sizeof(LinkRec<double>));
+  L.off_rb = o; o = al(o + (size_t)lb * rb);
   L.off_gsum = o; o = al(o + (size_t)n_ado * sizeof(double));
-  L.off_sp = o; o = al(o + (size_t)M * (D + 1) * sizeof(double));
-  L.off_sm = o; o = al(o + (size_t)M * (D + 1) * sizeof(double));
-  L.off_modes = o; o = al(o + (size_t)M * sizeof(ModeDev));
-  L.off_smo = o; o = al(o + (size_t)(n + 1) * sizeof(int));
   L.off_rec = o; o = al(o + (size_t)std::max<int64_t>(max_records, 1) * (n + 5) * sizeof(double));
   L.off_w = o; o = al(o + (size_t)n * sizeof(double));
   L.off_cnt = o; o = al(o + sizeof(int64_t));
@@ -210,9 +220,8 @@ extern "C" int heom_run_bytes(const heom_system *sys, const heom_hier *h, int pr
   int rc = check_system(sys, h, precision);
   if (rc) return rc;
   if (!bytes || max_records < 0) { set_error("heom_run_bytes: bad output pointer or max_records"); return HEOM_E_ARG; }
-  int Ep, Mp;
-  const int u_split = (precision == HEOM_FP64) ? 0 : (int)std::min<int64_t>(h->h.n, h->h.level_off[std::min(2, h->h.D + 1)]);
-  Layout L = make_layout(sys->n_states, h->h.M, h->h.D, h->h.n, u_split, precision, max_records, &Ep, &Mp);
+  int Ep;
+  Layout L = make_layout(sys->n_states, h->h, split_of(h->h, precision), precision, max_records, &Ep);
   *bytes = L.total;
   return HEOM_OK;
 }
@@ -266,10 +275,10 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   r->precision = precision;
   r->n = n; r->M = M; r->D = D; r->K = K; r->B = B;
   r->n_ado = h.n;
-  r->u_split = (precision == HEOM_FP64) ? 0 : (int)std::min<int64_t>(h.n, h.level_off[std::min(2, D + 1)]);
+  r->u_split = split_of(h, precision);
   r->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   r->max_records = max_records;
-  Layout L = make_layout(n, M, D, h.n, r->u_split, precision, max_records, &r->Ep, &r->Mp);
+  Layout L = make_layout(n, h, r->u_split, precision, max_records, &r->Ep);
   r->E = n * n;
   if (workspace_bytes < L.total) {
     delete r;
@@ -333,60 +342,74 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   }
   r->max_rate = D * gmax;
 
-  // modes grouped by state (stable), the order the kernel walks them
-  std::vector<int> perm(M);
-  for (int l = 0; l < M; ++l) perm[l] = l;
-  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b2) { return mstate[a] < mstate[b2]; });
-  std::vector<int> smo(n + 1, 0);
-  for (int l = 0; l < M; ++l) smo[mstate[l] + 1]++;
-  for (int s = 0; s < n; ++s) smo[s + 1] += smo[s];
-  std::vector<ModeDev> md(M);
+  // ---- rescaling factors s+_l(n), s-_l(n) (section "HEOM formalism", ADO rescaling)
   std::vector<double> sp((size_t)M * (D + 1)), sm((size_t)M * (D + 1));
-  for (int q = 0; q < M; ++q) {
-    const int l = perm[q];
-    md[q].state = mstate[l];
-    md[q].pad = 0;
-    md[q].c = cc[l];
-    md[q].lamnu = lnu[l];
+  for (int l = 0; l < M; ++l) {
     const double ac = std::fabs(cc[l]);
+    const bool scaled = sys->rescale && ac >= 1e-300;
     for (int nl = 0; nl <= D; ++nl) {
-      const bool scaled = sys->rescale && ac >= 1e-300;
-      sp[(size_t)q * (D + 1) + nl] = scaled ? std::sqrt((nl + 1) * ac) : 1.0;
-      sm[(size_t)q * (D + 1) + nl] = scaled ? std::sqrt(nl / ac) : (double)nl;
+      sp[(size_t)l * (D + 1) + nl] = scaled ? std::sqrt((nl + 1) * ac) : 1.0;
+      sm[(size_t)l * (D + 1) + nl] = scaled ? std::sqrt(nl / ac) : (double)nl;
     }
   }
 
-  // ---- tables, one row of Mp entries per ADO, modes in state order
-  const int Mp = r->Mp;
-  std::vector<int32_t> plusA, minusA;
-  std::vector<uint8_t> tupA;
+  // ---- per-ADO link records (CSR), decay sums
+  std::vector<int64_t> loff(h.n + 1, 0);
   std::vector<double> gs(h.n, 0.0);
+  std::vector<LinkRec<double>> rh;
+  std::vector<LinkRec<double>> rbd;
+  std::vector<LinkRec<float>> rbf;
+  const bool body_fp64 = precision == HEOM_FP64;
   try {
-    plusA.assign((size_t)h.n * Mp, -1);
-    minusA.assign((size_t)h.n * Mp, -1);
-    tupA.assign((size_t)h.n * Mp, 0);
+    const int64_t lh = count_links(h, 0, r->u_split);
+    rh.reserve(lh);
+    if (body_fp64) rbd.reserve(h.n_links - lh);
+    else rbf.reserve(h.n_links - lh);
   } catch (...) {
     delete r;
-    set_error("host allocation failed (tables)");
+    set_error("host allocation failed (link records)");
     return HEOM_E_NOMEM;
   }
+  int64_t nlink = 0;
   for (int64_t u = 0; u < h.n; ++u) {
+    loff[u] = nlink;
     double g = 0;
     for (int l = 0; l < M; ++l) g += h.tuples[(size_t)u * M + l] * gam[l];
     gs[u] = g;
-    for (int q = 0; q < M; ++q) {
-      const int l = perm[q];
-      plusA[(size_t)u * Mp + q] = h.plus[(size_t)u * M + l];
-      minusA[(size_t)u * Mp + q] = h.minus[(size_t)u * M + l];
-      tupA[(size_t)u * Mp + q] = h.tuples[(size_t)u * M + l];
+    for (int l = 0; l < M; ++l) {
+      const int nl = h.tuples[(size_t)u * M + l];
+      for (int dir = 0; dir < 2; ++dir) {
+        const int32_t v = dir ? h.minus[(size_t)u * M + l] : h.plus[(size_t)u * M + l];
+        if (v < 0) continue;
+        double re, im;
+        if (dir == 0) {  // up: R = i s+
+          re = 0.0;
+          im = sp[(size_t)l * (D + 1) + nl];
+        } else {  // down: R = s- (lamnu + i c)
+          const double f = sm[(size_t)l * (D + 1) + nl];
+          re = f * lnu[l];
+          im = f * cc[l];
+        }
+        if (u < r->u_split) {
+          rh.push_back(LinkRec<double>{v, mstate[l], 0, 0, re, im});
+        } else if (body_fp64) {
+          rbd.push_back(LinkRec<double>{v, mstate[l], 0, 0, re, im});
+        } else {
+          rbf.push_back(LinkRec<float>{v, mstate[l], (float)re, (float)im});
+        }
+        ++nlink;
+      }
     }
   }
+  loff[h.n] = nlink;
+  r->rec_split = loff[r->u_split];
 
   {  // algorithmic bytes and flops of one launch of the dominant kernel (ADOs u >= u_split)
     const double E = (double)n * n;
-    const double cs = (precision == HEOM_FP64) ? 16.0 : 8.0;
+    const double cs = body_fp64 ? 16.0 : 8.0;
     const double nb = (double)(h.n - r->u_split);
-    const double tab = nb * (r->Mp * 9.0 + 8.0);
+    const double nlb = (double)(nlink - r->rec_split);
+    const double tab = nb * 16.0 + nlb * (body_fp64 ? sizeof(LinkRec<double>) : sizeof(LinkRec<float>));
     r->bytes_stage_y = nb * 3.0 * E * cs + tab;
     r->bytes_stage_noy = nb * 2.0 * E * cs + tab;
     double up = 0, dn = 0;
@@ -399,14 +422,10 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   }
 
   char *base = reinterpret_cast<char *>(device_workspace);
-  r->plusA = reinterpret_cast<int32_t *>(base + L.off_plus);
-  r->minusA = reinterpret_cast<int32_t *>(base + L.off_minus);
-  r->tupA = reinterpret_cast<uint8_t *>(base + L.off_tup);
+  r->link_off = reinterpret_cast<int64_t *>(base + L.off_loff);
+  r->recs_head = base + L.off_rh;
+  r->recs_body = base + L.off_rb;
   r->gsum = reinterpret_cast<double *>(base + L.off_gsum);
-  r->sp_tab = reinterpret_cast<double *>(base + L.off_sp);
-  r->sm_tab = reinterpret_cast<double *>(base + L.off_sm);
-  r->modes = reinterpret_cast<ModeDev *>(base + L.off_modes);
-  r->state_mode_off = reinterpret_cast<int *>(base + L.off_smo);
   r->records = reinterpret_cast<double *>(base + L.off_rec);
   r->w_dev = reinterpret_cast<double *>(base + L.off_w);
   r->rec_count = reinterpret_cast<int64_t *>(base + L.off_cnt);
@@ -417,18 +436,18 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   std::vector<double> w(n, 0.0);
   if (dip_w) for (int i = 0; i < n; ++i) w[i] = dip_w[i];
   cudaStream_t st = r->stream;
-  ce = cudaMemcpyAsync(r->plusA, plusA.data(), plusA.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->minusA, minusA.data(), minusA.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->tupA, tupA.data(), tupA.size(), cudaMemcpyHostToDevice, st);
+  ce = cudaMemcpyAsync(r->link_off, loff.data(), loff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !rh.empty())
+    ce = cudaMemcpyAsync(r->recs_head, rh.data(), rh.size() * sizeof(rh[0]), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !rbd.empty())
+    ce = cudaMemcpyAsync(r->recs_body, rbd.data(), rbd.size() * sizeof(rbd[0]), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !rbf.empty())
+    ce = cudaMemcpyAsync(r->recs_body, rbf.data(), rbf.size() * sizeof(rbf[0]), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->gsum, gs.data(), gs.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->sp_tab, sp.data(), sp.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->sm_tab, sm.data(), sm.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->modes, md.data(), md.size() * sizeof(ModeDev), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->state_mode_off, smo.data(), smo.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->w_dev, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(r->rec_count, 0, sizeof(int64_t), st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(base + L.off_state[0], 0, L.head_bytes + L.body_bytes, st);
-  // the host vectors above are pageable: the copies complete before cudaMemcpyAsync returns
+  // the host vectors are pageable, so each copy has consumed its source when cudaMemcpyAsync returns
   if (ce != cudaSuccess) { delete r; return cuda_fail("workspace upload", ce); }
   // sigma_0 = rho(0): ADO 0 through the host-layout path
   std::vector<double> s0r((size_t)n * n), s0i((size_t)n * n, 0.0);
@@ -458,22 +477,16 @@ static StageCommon common_for(const heom_run *r, StateView zin, StateView y, Sta
   c.zin = zin;
   c.y = y;
   c.out = out;
-  c.plusA = r->plusA;
-  c.minusA = r->minusA;
-  c.tupA = r->tupA;
+  c.link_off = r->link_off;
+  c.recs_head = r->recs_head;
+  c.recs_body = r->recs_body;
+  c.rec_split = r->rec_split;
   c.gsum = r->gsum;
-  c.modes = r->modes;
-  c.state_mode_off = r->state_mode_off;
-  c.sp_tab = r->sp_tab;
-  c.sm_tab = r->sm_tab;
   c.E = r->E;
   c.Ep = r->Ep;
-  c.Mp = r->Mp;
   c.u_split = r->u_split;
   c.n_ado = (int)r->n_ado;
   c.n = r->n;
-  c.M = r->M;
-  c.D = r->D;
   c.cplx_h = r->cplx_h ? 1 : 0;
   return c;
 }

@@ -15,12 +15,23 @@ constexpr int kStageWarps = 4;  // warps per CTA of the stage kernel
 
 void set_error(const std::string &msg);
 
-// Per-mode constants, one record per mode l = b * (K + 1) + k, grouped by state on the device.
-struct ModeDev {
-  int state;      // s_l, the state coupled to the mode's bath
-  int pad;
-  double c;       // c(b, k), real
-  double lamnu;   // lambda_b nu_b for k = 0, else 0
+// One link of an ADO u to a neighbour v = n(u) +- e_l through a mode l of state s.  Only row s and
+// column s of v contribute to row s and column s of d sigma_u / dt: element (s, j != s) with
+// coefficient R, element (i != s, s) with conj(R), element (s, s) with 2 Re R, where
+//   up link (v = n + e_l):    R = i s+_l(n_l)            (s+ = sqrt((n_l + 1) |c_l|), or 1)
+//   down link (v = n - e_l):  R = s-_l(n_l) (lamnu_l + i c_l)   (s- = sqrt(n_l / |c_l|), or n_l)
+// (V^x contributes +1 on row s and -1 on column s, V^o +1 on both, 2 on the diagonal).
+template <typename T>
+struct LinkRec;
+template <>
+struct alignas(16) LinkRec<float> {
+  int v, s;
+  float re, im;
+};
+template <>
+struct alignas(16) LinkRec<double> {
+  int v, s, pad0, pad1;
+  double re, im;
 };
 
 // Hierarchy state storage of one RK4 copy: ADOs u < u_split ("head") as FP64 complex, ADOs
@@ -37,18 +48,15 @@ struct StageCommon {
   StateView zin;        // state the RHS is evaluated on (own tile and neighbour gathers)
   StateView y;          // Horner base y (head == nullptr && body == nullptr: none)
   StateView out;        // result y + ch * L zin (or ch * L zin)
-  const int32_t *plusA; // [n_ado][Mp], modes in state order, -1 = no link
-  const int32_t *minusA;
-  const uint8_t *tupA;  // [n_ado][Mp] n_l
-  const double *gsum;   // [n_ado] sum_l n_l gamma_l
-  const ModeDev *modes; // [M], ordered by state
-  const int *state_mode_off;  // [n + 1] modes of state s: [off[s], off[s+1])
-  const double *sp_tab;       // [M][D + 1] up factor  s+_l(n_l)
-  const double *sm_tab;       // [M][D + 1] down factor s-_l(n_l)
-  int E, Ep, Mp;        // N^2, body tile pitch, padded mode count (multiple of 16)
+  const int64_t *link_off;  // [n_ado + 1] first link record of each ADO
+  const void *recs_head;    // LinkRec<double> of ADOs u < u_split, indexed by link_off[u]
+  const void *recs_body;    // LinkRec<body compute type> of ADOs u >= u_split, by link_off[u] - rec_split
+  int64_t rec_split;        // link_off[u_split]
+  const double *gsum;       // [n_ado] sum_l n_l gamma_l
+  int E, Ep;                // N^2 and the body tile pitch (E rounded up to 16-byte tiles)
   int u_split, n_ado;
   int u_begin, u_end;   // ADO range of this launch
-  int n, M, D;
+  int n;
   int cplx_h;           // H has an imaginary part
 };
 

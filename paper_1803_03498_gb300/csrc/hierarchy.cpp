@@ -105,6 +105,9 @@ int build_hierarchy(int M, int D, Hierarchy *h, std::string *err) {
       }
     }
   }
+  int64_t k = 0;
+  for (size_t i = 0; i < h->plus.size(); ++i) k += (h->plus[i] >= 0) + (h->minus[i] >= 0);
+  h->n_links = k;
   return HEOM_OK;
 }
 

@@ -14,6 +14,7 @@ struct Hierarchy {
   std::vector<uint8_t> tuples;     // [n][M]
   std::vector<int32_t> plus;       // [n][M], -1 if |n| = D
   std::vector<int32_t> minus;      // [n][M], -1 if n_l = 0
+  int64_t n_links = 0;             // valid entries of plus and minus together
 };
 
 // Returns 0 or a negative HEOM_E_* code with *err filled.
