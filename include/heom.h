@@ -185,6 +185,35 @@ int64_t heom_run_launches(const heom_run *r);
 int heom_run_set_timing(heom_run *r, int enable);
 int heom_run_kernel_time(heom_run *r, double *ms, int64_t *launches, double *alg_bytes, double *alg_flops);
 
+/*
+ * heom_propagate_static -- one complete propagation that allocates no device memory, for callers
+ * that cannot call cudaMalloc (code running while its stream is being captured into a CUDA graph,
+ * plug-ins whose host application owns every device allocation, latency-critical paths that cannot
+ * afford the implicit synchronisation of cudaMalloc/cudaFree).  The paper has no counterpart; it
+ * is a deployment convenience around the same kernels as heom_run_create + heom_propagate +
+ * heom_observables.
+ *   Inputs (host, read during the call): sys, h, precision, sigma0_re/sigma0_im (n_states^2,
+ *   sigma0_im may be NULL), dip_w (n_states or NULL), dt_fs, n_steps, obs_stride, as for
+ *   heom_run_create and heom_propagate; cuda_stream as there.
+ *   Outputs (caller-owned host buffers): records_out [cap_records][n_states + 5] (the state at
+ *   the start, then one record every obs_stride steps; cap_records >= 1 + n_steps / obs_stride),
+ *   *written; sigma0_out_re/sigma0_out_im (n_states^2, both may be NULL) get the final sigma_0.
+ * The device workspace of the run (tables, state, the two intermediate RK4 copies and the records)
+ * lives in one library-owned static device array of 32 MiB (33554432 bytes) per GPU, which every GPU
+ * that loads the library holds until the process exits.  A run whose heom_run_bytes exceeds it is
+ * rejected with HEOM_E_NOMEM before any work.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Every call reuses the same array and zeroes what must start at zero; calls
+ * serialise on a lock within one process, and calls whose GPU work overlaps (for example from two
+ * processes sharing a context, or work still in flight on another stream) would race on it.  The
+ * call synchronises the stream before it returns.  Errors: those of heom_run_bytes,
+ * heom_run_create, heom_propagate and heom_observables, and HEOM_E_NOMEM as above.
+ */
+int heom_propagate_static(const heom_system *sys, const heom_hier *h, int precision, const double *sigma0_re,
+                          const double *sigma0_im, const double *dip_w, double dt_fs, int64_t n_steps,
+                          int64_t obs_stride, void *cuda_stream, double *records_out, int64_t cap_records,
+                          int64_t *written, double *sigma0_out_re, double *sigma0_out_im);
+
 #ifdef __cplusplus
 }
 #endif

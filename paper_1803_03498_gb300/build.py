@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libheom.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hierarchy.cpp", "heom_abi.cu"] + [f"stage_{p}_{g}.cu" for p in ("fp64", "fp32", "head") for g in "abcd"]
+SOURCES = ["hierarchy.cpp", "heom_abi.cu", "heom_static.cu"] + [f"stage_{p}_{g}.cu" for p in ("fp64", "fp32", "head") for g in "abcd"]
 HEADERS = ["hierarchy.h", "heom_internal.h", "stage_kernel.cuh"]
 
 

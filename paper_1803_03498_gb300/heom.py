@@ -24,7 +24,7 @@ ABI_SYMBOLS = [
     "heom_last_error", "heom_build_hierarchy", "heom_hier_destroy", "heom_hier_info", "heom_hier_export",
     "heom_run_bytes", "heom_run_create", "heom_run_destroy", "heom_propagate", "heom_record_len",
     "heom_observables", "heom_get_sigma0", "heom_get_ados", "heom_set_ados", "heom_rhs_eval", "heom_run_info",
-    "heom_run_launches", "heom_run_set_timing", "heom_run_kernel_time",
+    "heom_run_launches", "heom_run_set_timing", "heom_run_kernel_time", "heom_propagate_static",
 ]
 
 
@@ -84,6 +84,8 @@ def load():
     L.heom_run_launches.restype = i64
     L.heom_run_set_timing.argtypes = [vp, i]
     L.heom_run_kernel_time.argtypes = [vp, P(d), P(i64), P(d), P(d)]
+    L.heom_propagate_static.argtypes = [P(_System), vp, i, P(d), P(d), P(d), d, i64, i64, vp, P(d), i64, P(i64),
+                                        P(d), P(d)]
     for name in ABI_SYMBOLS:
         if name not in ("heom_last_error", "heom_run_launches"):
             getattr(L, name).restype = ctypes.c_int
@@ -254,3 +256,26 @@ class Run:
 
     def __del__(self):
         self.close()
+
+
+def propagate_static(system, rho0_re, rho0_im=None, precision="fp64", w=None, dt_fs=1.0, n_steps=0, obs_stride=1,
+                     terminator=True, rescale=True, hier: Hierarchy | None = None, stream=None):
+    """heom_propagate_static: a whole propagation whose device workspace is the library's static
+    array (no device allocation by the library or by this binding).  Returns (records, sigma_0)."""
+    L = load()
+    hier = hier if hier is not None else Hierarchy(system.n_modes, system.D)
+    sa = _SysArgs(system, terminator, rescale)
+    N = int(np.asarray(system.H).shape[0])
+    cap = 1 + (n_steps // obs_stride if obs_stride > 0 else 0)
+    rec = np.zeros((cap, N + 5))
+    s_re = np.zeros((N, N))
+    s_im = np.zeros((N, N))
+    r0 = np.ascontiguousarray(rho0_re, dtype=np.float64)
+    i0 = None if rho0_im is None else np.ascontiguousarray(rho0_im, dtype=np.float64)
+    wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    written = ctypes.c_int64()
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(L.heom_propagate_static(ctypes.byref(sa.s), hier._h, PRECISIONS[precision], _dp(r0), _dp(i0), _dp(wv),
+                                   float(dt_fs), int(n_steps), int(obs_stride), st, _dp(rec), cap,
+                                   ctypes.byref(written), _dp(s_re), _dp(s_im)))
+    return rec[: written.value].copy(), s_re + 1j * s_im
