@@ -56,6 +56,7 @@ struct heom_run {
   // host copies of the per-run constants (rad/fs)
   std::vector<double> H, Hi;         // shifted Re H, Im H
   bool cplx_h = false;
+  bool herm = false;                 // every ADO Hermitian (Hermitian H and data; paper gauge)
   std::vector<double> term;          // per state
   double max_rate = 0;               // D * max gamma
   // device
@@ -78,7 +79,8 @@ struct heom_run {
   bool pending = false;              // a begin event was recorded for the current launch
   std::vector<cudaEvent_t> ev;       // pairs
   double timed_bytes = 0, timed_flops = 0;
-  double bytes_stage_y = 0, bytes_stage_noy = 0, flops_stage = 0;  // per launch over the body range
+  double bytes_stage_y = 0, bytes_stage_noy = 0;  // per launch over the body range
+  double flops_gen = 0, flops_herm = 0;             // per launch: general and Hermitian forms
   ~heom_run() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
   }
@@ -305,6 +307,14 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     r->Hi[i] = sys->H_im ? kCmToRadFs * sys->H_im[i] : 0.0;
     if (r->Hi[i] != 0.0) r->cplx_h = true;
   }
+  // With a Hermitian H the real coefficients of the paper's gauge map Hermitian ADOs to Hermitian
+  // ADOs; the flag stays on while every uploaded ADO (rho(0) below) is exactly Hermitian.
+  r->herm = true;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (sys->H_re[i * n + j] != sys->H_re[j * n + i] ||
+          (sys->H_im && sys->H_im[i * n + j] != -sys->H_im[j * n + i]))
+        r->herm = false;
 
   // ---- Matsubara coefficients of Eq. HEOM (Drude-Lorentz, Omega = 0), terminator and rescaling
   std::vector<double> gam(M), cc(M), lnu(M);
@@ -418,7 +428,11 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
         up += h.plus[(size_t)u * M + l] >= 0;
         dn += h.minus[(size_t)u * M + l] >= 0;
       }
-    r->flops_stage = nb * ((r->cplx_h ? 16.0 : 8.0) * n * E + 8.0 * E) + up * 8.0 * (n - 1) + dn * 8.0 * (2 * n - 1);
+    // the Hermitian form computes H s only (s H = (H s)^dagger): half the commutator flops
+    const double comm = (r->cplx_h ? 16.0 : 8.0) * n * E;
+    const double links = up * 8.0 * (n - 1) + dn * 8.0 * (2 * n - 1);
+    r->flops_gen = nb * (comm + 8.0 * E) + links;
+    r->flops_herm = nb * (0.5 * comm + 8.0 * E) + links;
   }
 
   char *base = reinterpret_cast<char *>(device_workspace);
@@ -488,6 +502,7 @@ static StageCommon common_for(const heom_run *r, StateView zin, StateView y, Sta
   c.n_ado = (int)r->n_ado;
   c.n = r->n;
   c.cplx_h = r->cplx_h ? 1 : 0;
+  c.herm = r->herm ? 1 : 0;
   return c;
 }
 
@@ -512,7 +527,7 @@ static int timed_end(heom_run *r, double bytes) {
   cudaError_t e = cudaEventRecord(r->ev.back(), r->stream);
   if (e != cudaSuccess) return cuda_fail("timing event record", e);
   r->timed_bytes += bytes;
-  r->timed_flops += r->flops_stage;
+  r->timed_flops += r->herm ? r->flops_herm : r->flops_gen;
   return HEOM_OK;
 }
 
@@ -687,6 +702,18 @@ static int io_range(heom_run *r, StateView state, int64_t u0, int64_t count, dou
 
 extern "C" int heom_set_ados(heom_run *r, int64_t u0, int64_t count, const double *re, const double *im) {
   if (!r) { set_error("heom_set_ados: NULL run"); return HEOM_E_ARG; }
+  if (r->herm && re && im) {  // a non-Hermitian ADO switches the run to the general kernels for good
+    const int n = r->n;
+    for (int64_t c = 0; c < count && r->herm; ++c) {
+      const double *a = re + c * n * n, *b = im + c * n * n;
+      for (int i = 0; i < n && r->herm; ++i)
+        for (int j = i; j < n; ++j)
+          if (a[i * n + j] != a[j * n + i] || b[i * n + j] != -b[j * n + i]) {
+            r->herm = false;
+            break;
+          }
+    }
+  }
   return io_range(r, r->y, u0, count, const_cast<double *>(re), const_cast<double *>(im), true);
 }
 

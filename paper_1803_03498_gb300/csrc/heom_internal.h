@@ -58,6 +58,7 @@ struct StageCommon {
   int u_begin, u_end;   // ADO range of this launch
   int n;
   int cplx_h;           // H has an imaginary part
+  int herm;             // every ADO is Hermitian: gather row s only, and s H = (H s)^dagger
 };
 
 template <typename CT>

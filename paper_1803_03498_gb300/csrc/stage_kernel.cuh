@@ -101,8 +101,9 @@ __device__ __forceinline__ void issue_tiles(const typename Cplx<CT>::type *src_r
 }
 
 // Gathers row s and column s of the neighbours of nrec link records into gbuf:
-// [slot][0..N) = v_{s, 0..N-1}, [slot][N..2N) = v_{0..N-1, s}.  Same-precision elements go by
-// cp.async (one group is committed); elements of the other precision region are converted.
+// [slot][0..N) = v_{s, 0..N-1}, [slot][N..2N) = v_{0..N-1, s} (row only for Hermitian ADOs).
+// Same-precision elements go by cp.async (one group is committed); elements of the other precision
+// region are converted.
 template <int N, typename CT, typename BT>
 __device__ __forceinline__ void issue_gathers(const StageCommon &c, const LinkRec<CT> *rec, int nrec,
                                               typename Cplx<CT>::type *gbuf, int lane) {
@@ -110,8 +111,10 @@ __device__ __forceinline__ void issue_gathers(const StageCommon &c, const LinkRe
   using C2 = typename Cplx<CT>::type;
   using B2 = typename Cplx<BT>::type;
   const B2 *zb = reinterpret_cast<const B2 *>(c.zin.body);
-  for (int t = lane; t < nrec * 2 * N; t += 32) {
-    const int sl = t / (2 * N), el = t - sl * 2 * N;
+  const int per = c.herm ? N : 2 * N;  // Hermitian ADOs: column s is conj(row s)
+  for (int t0 = lane; t0 < nrec * per; t0 += 32) {
+    const int sl = t0 / per, el = t0 - sl * per;
+    const int t = sl * 2 * N + el;
     const int s = rec[sl].s, v = rec[sl].v;
     const int e = (el < N) ? (s * N + el) : ((el - N) * N + s);
     if (v >= c.u_split) {
@@ -148,8 +151,8 @@ __device__ __forceinline__ void issue_gathers(const StageCommon &c, const LinkRe
 // within one k; the warp synchronises between k.
 template <int N, typename CT, typename BT>
 __device__ __forceinline__ void apply_links(const LinkRec<CT> *rec, int64_t blo, int nrec, int64_t my_lo,
-                                            int64_t my_hi, bool active, int li, typename Cplx<CT>::type *ot,
-                                            const typename Cplx<CT>::type *gbuf) {
+                                            int64_t my_hi, bool active, int li, bool herm,
+                                            typename Cplx<CT>::type *ot, const typename Cplx<CT>::type *gbuf) {
   using C2 = typename Cplx<CT>::type;
   const int64_t a_lo = max(my_lo, blo), a_hi = min(my_hi, blo + nrec);
   const int my_cnt = active ? (int)max((int64_t)0, a_hi - a_lo) : 0;
@@ -167,8 +170,14 @@ __device__ __forceinline__ void apply_links(const LinkRec<CT> *rec, int64_t blo,
         o.y = fma(2 * r.re, v.y, o.y);
         ot[s * N + s] = o;
       } else {
-        const C2 vr = gv[li];      // element (s, li) of the neighbour: coefficient R
-        const C2 vc = gv[N + li];  // element (li, s): coefficient conj(R)
+        const C2 vr = gv[li];  // element (s, li) of the neighbour: coefficient R
+        C2 vc;                 // element (li, s): coefficient conj(R)
+        if (herm) {
+          vc.x = vr.x;
+          vc.y = -vr.y;
+        } else {
+          vc = gv[N + li];
+        }
         C2 o1 = ot[s * N + li];
         o1.x = fma(r.re, vr.x, fma(-r.im, vr.y, o1.x));
         o1.y = fma(r.re, vr.y, fma(r.im, vr.x, o1.y));
@@ -267,10 +276,17 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
 
     {  // commutator -i (H s - s H), decay and terminator of row li
       const C2 *zt = zt_all + la * EPO;
-      CT rr[N], ri[N];
+      const bool herm = c.herm != 0;
+      CT rr[N], ri[N];  // row li of -i (H s - s H): real and imaginary parts
+      C2 zr[N];         // own row s_{li, .}
       if (active) {
 #pragma unroll
-        for (int j = 0; j < N; ++j) { rr[j] = 0; ri[j] = 0; }
+        for (int j = 0; j < N; ++j) {
+          rr[j] = 0;
+          ri[j] = 0;
+          zr[j] = zt[li * N + j];
+        }
+        // -i (H s)
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           const CT h = S::kRowRegs ? Hrow[S::kRowRegs ? k : 0] : a.H[li * kMaxStates + k];
@@ -293,39 +309,73 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
             }
           }
         }
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          const C2 zk = zt[li * N + k];
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const CT h = a.H[k * kMaxStates + j];
-            rr[j] = fma(-zk.y, h, rr[j]);
-            ri[j] = fma(zk.x, h, ri[j]);
-          }
-        }
-        if constexpr (CPLX) {  // imaginary part of H
+        if constexpr (CPLX) {  // imaginary part of H in -i (H s)
 #pragma unroll
           for (int k = 0; k < N; ++k) {
             const CT h = a.Hi[li * kMaxStates + k];
-            const C2 zk = zt[li * N + k];
 #pragma unroll
             for (int j = 0; j < N; ++j) {
               const C2 z = zt[k * N + j];
               rr[j] = fma(h, z.x, rr[j]);
               ri[j] = fma(h, z.y, ri[j]);
-              const CT h2 = a.Hi[k * kMaxStates + j];
-              rr[j] = fma(-zk.x, h2, rr[j]);
-              ri[j] = fma(-zk.y, h2, ri[j]);
             }
           }
         }
+        if (!herm) {  // + i (s H)
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const C2 zk = zr[k];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+              const CT h = a.H[k * kMaxStates + j];
+              rr[j] = fma(-zk.y, h, rr[j]);
+              ri[j] = fma(zk.x, h, ri[j]);
+            }
+          }
+          if constexpr (CPLX) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              const C2 zk = zr[k];
+#pragma unroll
+              for (int j = 0; j < N; ++j) {
+                const CT h2 = a.Hi[k * kMaxStates + j];
+                rr[j] = fma(-zk.x, h2, rr[j]);
+                ri[j] = fma(-zk.y, h2, ri[j]);
+              }
+            }
+          }
+        }
+      }
+      if (herm) {
+        // s and H Hermitian: s H = (H s)^dagger, so -i (H s - s H)_ij = -i (P_ij - conj(P_ji)) with
+        // P = H s; in the (rr, ri) = -i P form that is (rr_ij + rr_ji, ri_ij - ri_ji).
+        __syncwarp();  // every lane is done reading the tile
+        if (active) {
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            C2 w;
+            w.x = rr[j];
+            w.y = ri[j];
+            zt_all[la * EPO + li * N + j] = w;
+          }
+        }
+        __syncwarp();
+        if (active) {
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const C2 t = zt_all[la * EPO + j * N + li];
+            rr[j] += t.x;
+            ri[j] -= t.y;
+          }
+        }
+      }
+      if (active) {  // decay and terminator
         const CT gsv = (CT)c.gsum[u0 + la];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const C2 zij = zt[li * N + j];
           const CT f = gsv + ((j != li) ? (term_i + a.term[j]) : (CT)0);
-          rr[j] = fma(-f, zij.x, rr[j]);
-          ri[j] = fma(-f, zij.y, ri[j]);
+          rr[j] = fma(-f, zr[j].x, rr[j]);
+          ri[j] = fma(-f, zr[j].y, ri[j]);
         }
       }
       __syncwarp();  // every lane is done reading the tile: it becomes the output buffer
@@ -342,7 +392,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
     cp_async_wait<0>();  // gathers, y and the next chunk's copies have landed
     __syncwarp();
     C2 *ot = zt_all + la * EPO;
-    apply_links<N, CT, BT>(rec, lo, nrec, my_lo, my_hi, active, li, ot, gbuf);
+    apply_links<N, CT, BT>(rec, lo, nrec, my_lo, my_hi, active, li, c.herm != 0, ot, gbuf);
     for (int64_t blo = lo + nrec; blo < hi; blo += kRecCap) {  // further link batches
       __syncwarp();
       const int nr = (int)min(hi - blo, (int64_t)kRecCap);
@@ -353,7 +403,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
       issue_gathers<N, CT, BT>(c, rec, nr, gbuf, lane);
       cp_async_wait<0>();
       __syncwarp();
-      apply_links<N, CT, BT>(rec, blo, nr, my_lo, my_hi, active, li, ot, gbuf);
+      apply_links<N, CT, BT>(rec, blo, nr, my_lo, my_hi, active, li, c.herm != 0, ot, gbuf);
     }
     __syncwarp();
     // y + ch * rhs over the chunk's contiguous tiles, 16 bytes per access

@@ -142,6 +142,33 @@ def test_rhs_eval_small_random_state():
     assert np.array_equal(sre, re) and np.array_equal(sim, im)
 
 
+def hermitian(re, im):
+    """Hermitian part of every tile: (A + A^dagger) / 2."""
+    return 0.5 * (re + np.transpose(re, (0, 2, 1))), 0.5 * (im - np.transpose(im, (0, 2, 1)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_rhs_eval_hermitian_random_state(precision):
+    """A dense random Hermitian state takes the Hermitian kernels (row-only gathers, s H = (H s)^dagger);
+    every ADO of one RHS evaluation against the oracle's general formula."""
+    pop, dips = wl.fmo_like()
+    m = oracle_for(pop.system)
+    re, im = hermitian(*wl.random_state(m.n_ado, m.N, seed=15))
+    from paper_1803_03498_gb300 import heom
+    r = heom.Run(pop.system, pop.rho0_re, pop.rho0_im, precision=precision, max_records=2)
+    r.set_ados(0, re, im)
+    if precision == "fp32_mixed":
+        re, im = r.get_ados(0, m.n_ado)
+    ore, oim = m.rhs(re, im)
+    gre, gim = r.rhs_eval(0, m.n_ado)
+    scale = np.max(np.abs(ore + 1j * oim))
+    tol = 1e-14 * scale * 10 if precision == "fp64" else 2e-5 * scale
+    assert np.max(np.abs((gre - ore) + 1j * (gim - oim))) <= tol
+    # the result is exactly Hermitian
+    g = gre + 1j * gim
+    assert np.array_equal(g, np.conj(np.transpose(g, (0, 2, 1))))
+
+
 def sample_ados(level_offsets, n_ado, rng, n_random=300):
     us = set()
     for off in level_offsets[:-1]:
@@ -155,8 +182,9 @@ def sample_ados(level_offsets, n_ado, rng, n_random=300):
     return np.array(sorted(us), dtype=np.int64)
 
 
+@pytest.mark.parametrize("herm", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
-def test_lhcii_full_size_rhs_sampled(precision):
+def test_lhcii_full_size_rhs_sampled(precision, herm):
     """Full LHCII-like hierarchy (1,344,904 ADOs of 14 x 14): one RHS evaluation of a dense random
     state with the benchmark's kernels and launch configuration, checked on sampled ADOs (every
     level boundary and 300 random ADOs) against the oracle's per-ADO right-hand side."""
@@ -164,6 +192,8 @@ def test_lhcii_full_size_rhs_sampled(precision):
     p = wl.lhcii_like()
     m = oracle_for(p.system)
     re, im = wl.random_state(m.n_ado, m.N, seed=9, scale=0.1)
+    if herm:
+        re, im = hermitian(re, im)
     r = heom.Run(p.system, p.rho0_re, p.rho0_im, precision=precision, max_records=2)
     r.set_ados(0, re, im)
     if precision == "fp32_mixed":
