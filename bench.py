@@ -44,6 +44,30 @@ def _peaks():
 FP64_PEAK_TFLOPS = 1.2  # measured FP64 FMA throughput of GB300 (152 SMs x 4 flop/clk x ~1.97 GHz)
 
 
+def _traffic():
+    """DRAM bytes per launch of the dominant kernels from the committed ncu summary, or None when
+    the kernel sources changed since those counters were taken."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1803_03498_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("stage_kernel.cuh", "heom_abi.cu"):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    vals = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "stage_kernel_lhcii_dram.md")) as fh:
+            for line in fh:
+                p = line.split()
+                if len(p) == 2 and (p[0].startswith("traffic_") or p[0] == "source_sha256_16"):
+                    vals[p[0]] = p[1]
+    except OSError:
+        return None, None
+    if vals.get("source_sha256_16") != h.hexdigest()[:16]:
+        return None, None
+    return float(vals["traffic_fp32_mixed_body_bytes_per_launch"]), float(vals["traffic_fp64_bytes_per_launch"])
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
 
@@ -282,6 +306,7 @@ def main():
     ms_max = _max_over_ranks(ms, ws)
     value = ws * n_ado * 4 * args.steps / (ms_max / 1000.0)
     hbm_peak, peak_src = _peaks()
+    traffic32, traffic64 = _traffic()
     ach = kt["alg_bytes"] / (kt["ms"] / 1000.0) / 1e9 if kt["ms"] > 0 else 0.0
 
     # FP64 variant
@@ -313,14 +338,15 @@ def main():
             "clocks": clk,
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": ach / hbm_peak, "traffic": None,
+                         "frac": ach / hbm_peak, "traffic": traffic32,
+                         "alg_bytes_per_launch": kt["alg_bytes"] / max(kt["launches"], 1),
                          "kernel": "stage_kernel<14,float,float> (levels >= 2)",
                          "peak_source": peak_src, "timed_launches": kt["launches"],
                          "avg_launch_ms": kt["ms"] / max(kt["launches"], 1)},
             "fp64": {"value": v64, "unit": UNIT, "steps": f64_steps, "ms_per_step": ms64 / f64_steps,
                      "mixed_over_fp64": value / v64,
                      "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                  "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": None,
+                                  "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": traffic64,
                                   "kernel": "stage_kernel<14,double,double>",
                                   "avg_launch_ms": kt64["ms"] / max(kt64["launches"], 1)}},
             "mixed_vs_fp64_pop_diff": pop_diff,
