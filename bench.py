@@ -191,6 +191,52 @@ def time_e2e(prop, precision, steps, hier):
     return (t1 - t0), h2d / steps, d2h / steps
 
 
+def time_batch(steps=20, per_launch=10):
+    """The ragged batch (64 systems x 3 dipole orientations = 192 runs, N+1 in 3..17, D in 3..5,
+    K in 0..1, mixed precision): all runs in one CUDA graph per `per_launch` steps, against the same
+    runs propagated one after another with heom_propagate.  Returns a dict."""
+    import torch
+
+    from paper_1803_03498_gb300 import heom
+    from paper_1803_03498_gb300 import workloads as wl
+
+    props = wl.ragged_batch()
+    dt = props[0].dt_fs
+    n_ado = sum(p.system.n_ado for p in props)
+    runs = [heom.Run(p.system, p.rho0_re, p.rho0_im, precision="fp32_mixed", w=p.w,
+                     max_records=3 * steps // per_launch + 4) for p in props]
+    t0 = time.perf_counter()
+    b = heom.Batch(runs, dt, per_launch, per_launch)
+    t_capture = time.perf_counter() - t0
+    b.launch(1)  # warm-up
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.launch(steps // per_launch)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    # sequential: one run after the other, each run's steps enqueued as separate launches
+    for r in runs:
+        r.propagate(dt, 1, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in runs:
+        r.propagate(dt, steps, per_launch)
+        torch.cuda.synchronize()
+    ms_seq = (time.perf_counter() - t0) * 1000
+    b.close()
+    for r in runs:
+        r.close()
+    evals = n_ado * 4 * (steps // per_launch) * per_launch
+    return {"workload": "ragged batch: 64 systems x 3 dipole orientations = 192 runs, 2,597,400 ADOs, "
+                        "N+1 in 3..17, D in 3..5, K in 0..1, fp32_mixed, dt=0.5 fs",
+            "value": evals / (ms_batch / 1000), "unit": UNIT, "steps": steps, "ms_per_step": ms_batch / steps,
+            "sequential_value": evals / (ms_seq / 1000), "speedup_vs_sequential": ms_seq / ms_batch,
+            "graph": f"one CUDA graph per {per_launch} steps of all runs (capture + instantiate {t_capture:.2f} s)"}
+
+
 def cpu_baseline(prop, seconds=12.0, seed=1):
     """The CPU oracle (single thread, as it stands) on a bounded sample of the same workload: the
     right-hand side of randomly chosen ADOs of the full hierarchy, on a random dense state."""
@@ -261,6 +307,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch leg")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 variant (0: steps/20)")
     ap.add_argument("--depth", type=int, default=0, help="override the hierarchy depth (profiling cases)")
     ap.add_argument("--only", default="", choices=["", "mixed", "fp64"],
@@ -353,6 +400,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "what": "heom_run_create from host arrays + propagate + observables to host, wall clock"},
         }
+        if not args.no_batch:
+            line["batch"] = time_batch()
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prop)
         print(json.dumps(line), flush=True)

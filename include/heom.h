@@ -186,6 +186,26 @@ int heom_run_set_timing(heom_run *r, int enable);
 int heom_run_kernel_time(heom_run *r, double *ms, int64_t *launches, double *alg_bytes, double *alg_flops);
 
 /*
+ * Ragged batches (many independent propagations of different sizes advanced together).
+ * heom_batch_create captures steps_per_launch RK4 steps of every run (each run's stage launches on
+ * one of up to 32 library-created streams, so small runs execute concurrently; one observable record
+ * every obs_stride steps, obs_stride dividing steps_per_launch, 0 = none) into one CUDA graph.  The
+ * runs must be on the current device, with timing off; the call synchronises their streams first.
+ * heom_batch_launch replays the graph n_launches times on a stream of the batch's own (ordered after
+ * work already enqueued on every run's stream; later work on a run's stream is ordered after it) and
+ * advances each run's step and record counters; HEOM_E_NOMEM if a run's records would overflow
+ * max_records.  Results are those of heom_propagate with the same steps (same kernels, same order
+ * per run).  heom_batch_destroy synchronises the batch's stream and frees the graph (the runs stay).
+ * The paper runs independent propagations (rotational averages, polarisation sequences) side by
+ * side (section "Distributed memory HEOM implementation"); this is that, on one GPU.
+ */
+typedef struct heom_batch heom_batch;
+int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs, int64_t steps_per_launch, int64_t obs_stride,
+                      heom_batch **out);
+int heom_batch_launch(heom_batch *b, int64_t n_launches);
+int heom_batch_destroy(heom_batch *b);
+
+/*
  * heom_propagate_static -- one complete propagation that allocates no device memory, for callers
  * that cannot call cudaMalloc (code running while its stream is being captured into a CUDA graph,
  * plug-ins whose host application owns every device allocation, latency-critical paths that cannot

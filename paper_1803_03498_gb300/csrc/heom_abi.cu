@@ -823,3 +823,154 @@ __global__ void gather_kernel(StateView src, int Ep, int u_split, int body_fp32,
 }
 
 }  // namespace heom
+
+// ------------------------------------------------------------------------------------------------
+// ragged batches: the stage launches of many runs, each on one of a pool of streams, captured into
+// one CUDA graph that advances every run by steps_per_launch RK4 steps per replay.
+
+struct heom_batch {
+  std::vector<heom_run *> runs;
+  std::vector<cudaStream_t> pool;
+  std::vector<cudaEvent_t> ev;  // fork/join events of the capture, then per-launch join events
+  cudaStream_t origin = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double dt = 0;
+  int64_t steps_per_launch = 0, obs_stride = 0;
+  std::vector<int64_t> launches_per_replay;
+  ~heom_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaStream_t s : pool) cudaStreamDestroy(s);
+    if (origin) cudaStreamDestroy(origin);
+  }
+};
+
+extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs, int64_t steps_per_launch,
+                                 int64_t obs_stride, heom_batch **out) {
+  if (!out || !runs || n_runs < 1 || !(dt_fs > 0) || steps_per_launch < 1 || obs_stride < 0 ||
+      (obs_stride > 0 && steps_per_launch % obs_stride != 0)) {
+    set_error("heom_batch_create: need runs, n_runs >= 1, dt_fs > 0, steps_per_launch >= 1, "
+              "obs_stride >= 0 dividing steps_per_launch");
+    return HEOM_E_ARG;
+  }
+  *out = nullptr;
+  for (int i = 0; i < n_runs; ++i) {
+    if (!runs[i]) { set_error("heom_batch_create: NULL run"); return HEOM_E_ARG; }
+    if (dt_fs * runs[i]->max_rate > 2.5) {
+      set_error("heom_batch_create: dt_fs * depth * max gamma > 2.5 for a run (RK4 unstable)");
+      return HEOM_E_ARG;
+    }
+    if (runs[i]->timing) { set_error("heom_batch_create: switch timing off on every run first"); return HEOM_E_STATE; }
+  }
+  heom_batch *b = new (std::nothrow) heom_batch;
+  if (!b) { set_error("host allocation failed"); return HEOM_E_NOMEM; }
+  b->runs.assign(runs, runs + n_runs);
+  b->dt = dt_fs;
+  b->steps_per_launch = steps_per_launch;
+  b->obs_stride = obs_stride;
+  const int P = std::min(n_runs, 32);
+  // the graph is captured on (and later launched on) a stream of its own: the runs' streams may be
+  // the legacy default stream, which cannot be captured
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: origin stream", e); }
+  for (int p = 0; p < P && e == cudaSuccess; ++p) {
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->pool.push_back(s);
+  }
+  for (int k = 0; k < P + 1 && e == cudaSuccess; ++k) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ev.push_back(ev);
+  }
+  if (e != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: streams/events", e); }
+  // wait for everything already enqueued on the runs' own streams, then capture
+  for (heom_run *r : b->runs) {
+    e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: run stream", e); }
+  }
+  e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: begin capture", e); }
+  int rc = HEOM_OK;
+  e = cudaEventRecord(b->ev[P], b->origin);
+  for (int p = 0; p < P && e == cudaSuccess; ++p) e = cudaStreamWaitEvent(b->pool[p], b->ev[P], 0);
+  b->launches_per_replay.assign(n_runs, 0);
+  const double h = dt_fs;
+  for (int i = 0; i < n_runs && e == cudaSuccess && rc == HEOM_OK; ++i) {
+    heom_run *r = b->runs[i];
+    cudaStream_t own = r->stream;
+    const int64_t l0 = r->launches, rec0 = r->records_host, max0 = r->max_records;
+    r->stream = b->pool[i % P];
+    r->max_records = INT64_MAX;  // counters are restored below; launches advance them
+    for (int64_t s = 0; s < steps_per_launch && rc == HEOM_OK; ++s) {
+      if ((rc = run_stage(r, r->y, r->y, r->zA, h / 4))) break;
+      if ((rc = run_stage(r, r->zA, r->y, r->zB, h / 3))) break;
+      if ((rc = run_stage(r, r->zB, r->y, r->zA, h / 2))) break;
+      if ((rc = run_stage(r, r->zA, r->y, r->y, h))) break;
+      if (obs_stride > 0 && (s + 1) % obs_stride == 0) rc = enqueue_record(r);
+    }
+    b->launches_per_replay[i] = r->launches - l0;
+    r->launches = l0;
+    r->records_host = rec0;
+    r->max_records = max0;
+    r->stream = own;
+  }
+  for (int p = 0; p < P && e == cudaSuccess; ++p) {
+    e = cudaEventRecord(b->ev[p], b->pool[p]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev[p], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(b->origin, &g);
+  if (rc != HEOM_OK) { if (g) cudaGraphDestroy(g); delete b; return rc; }
+  if (e == cudaSuccess) e = ee;
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); delete b; return cuda_fail("heom_batch_create: capture", e); }
+  b->graph = g;
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: instantiate", e); }
+  *out = b;
+  return HEOM_OK;
+}
+
+extern "C" int heom_batch_launch(heom_batch *b, int64_t n_launches) {
+  if (!b || n_launches < 0) { set_error("heom_batch_launch: bad arguments"); return HEOM_E_ARG; }
+  const int64_t recs = b->obs_stride > 0 ? b->steps_per_launch / b->obs_stride : 0;
+  for (heom_run *r : b->runs)
+    if (r->records_host + recs * n_launches > r->max_records) {
+      set_error("heom_batch_launch: observable records of a run would exceed its max_records");
+      return HEOM_E_NOMEM;
+    }
+  // order after work already enqueued on the runs' own streams (each distinct stream once)
+  cudaError_t e = cudaSuccess;
+  std::vector<cudaStream_t> seen;
+  for (heom_run *r : b->runs) {
+    if (std::find(seen.begin(), seen.end(), r->stream) != seen.end()) continue;
+    seen.push_back(r->stream);
+    e = cudaEventRecord(b->ev[0], r->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev[0], 0);
+    if (e != cudaSuccess) return cuda_fail("heom_batch_launch: ordering", e);
+  }
+  for (int64_t k = 0; k < n_launches; ++k) {
+    e = cudaGraphLaunch(b->exec, b->origin);
+    if (e != cudaSuccess) return cuda_fail("heom_batch_launch: graph launch", e);
+  }
+  // later calls on a run's own stream see the batch's work
+  e = cudaEventRecord(b->ev[0], b->origin);
+  for (size_t k = 0; k < seen.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(seen[k], b->ev[0], 0);
+  if (e != cudaSuccess) return cuda_fail("heom_batch_launch: join", e);
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    heom_run *r = b->runs[i];
+    r->steps_done += n_launches * b->steps_per_launch;
+    r->t_fs += (double)(n_launches * b->steps_per_launch) * b->dt;
+    r->records_host += recs * n_launches;
+    r->launches += n_launches * b->launches_per_replay[i];
+  }
+  return HEOM_OK;
+}
+
+extern "C" int heom_batch_destroy(heom_batch *b) {
+  if (b) cudaStreamSynchronize(b->origin);
+  delete b;
+  return HEOM_OK;
+}

@@ -211,6 +211,14 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
   const bool lane_ok = la < A;
   const bool has_y = (c.y.head != nullptr) || (c.y.body != nullptr);
   const CT term_i = lane_ok ? a.term[li] : (CT)0;
+  // terminator Delta_i + Delta_j of row li (0 on the diagonal), precomputed in FP64 where every FP64
+  // add costs pipe time; FP32 recomputes it (the registers are worth more there)
+  constexpr bool kTsum = sizeof(CT) == 8;
+  CT tsum[kTsum ? N : 1];
+  if constexpr (kTsum) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) tsum[j] = (lane_ok && j != li) ? term_i + a.term[j] : (CT)0;
+  }
   CT Hrow[S::kRowRegs ? N : 1];
   if constexpr (S::kRowRegs) {
 #pragma unroll
@@ -373,7 +381,9 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
         const CT gsv = (CT)c.gsum[u0 + la];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const CT f = gsv + ((j != li) ? (term_i + a.term[j]) : (CT)0);
+          CT f;
+          if constexpr (kTsum) f = gsv + tsum[kTsum ? j : 0];
+          else f = gsv + ((j != li) ? (term_i + a.term[j]) : (CT)0);
           rr[j] = fma(-f, zr[j].x, rr[j]);
           ri[j] = fma(-f, zr[j].y, ri[j]);
         }

@@ -25,6 +25,7 @@ ABI_SYMBOLS = [
     "heom_run_bytes", "heom_run_create", "heom_run_destroy", "heom_propagate", "heom_record_len",
     "heom_observables", "heom_get_sigma0", "heom_get_ados", "heom_set_ados", "heom_rhs_eval", "heom_run_info",
     "heom_run_launches", "heom_run_set_timing", "heom_run_kernel_time", "heom_propagate_static",
+    "heom_batch_create", "heom_batch_launch", "heom_batch_destroy",
 ]
 
 
@@ -84,6 +85,9 @@ def load():
     L.heom_run_launches.restype = i64
     L.heom_run_set_timing.argtypes = [vp, i]
     L.heom_run_kernel_time.argtypes = [vp, P(d), P(i64), P(d), P(d)]
+    L.heom_batch_create.argtypes = [P(vp), i, d, i64, i64, P(vp)]
+    L.heom_batch_launch.argtypes = [vp, i64]
+    L.heom_batch_destroy.argtypes = [vp]
     L.heom_propagate_static.argtypes = [P(_System), vp, i, P(d), P(d), P(d), d, i64, i64, vp, P(d), i64, P(i64),
                                         P(d), P(d)]
     for name in ABI_SYMBOLS:
@@ -253,6 +257,30 @@ class Run:
         if getattr(self, "_r", None) is not None and self._r.value:
             load().heom_run_destroy(self._r)
             self._r = ctypes.c_void_p()
+
+    def __del__(self):
+        self.close()
+
+
+class Batch:
+    """heom_batch_create: one CUDA graph advancing every run by steps_per_launch RK4 steps."""
+
+    def __init__(self, runs, dt_fs: float, steps_per_launch: int, obs_stride: int = 1):
+        L = load()
+        self.runs = list(runs)  # keeps the runs (and their workspaces) alive
+        arr = (ctypes.c_void_p * len(self.runs))(*[r._r.value for r in self.runs])
+        self._b = ctypes.c_void_p()
+        _check(L.heom_batch_create(arr, len(self.runs), float(dt_fs), int(steps_per_launch), int(obs_stride),
+                                   ctypes.byref(self._b)))
+        self.steps_per_launch = int(steps_per_launch)
+
+    def launch(self, n_launches: int = 1):
+        _check(load().heom_batch_launch(self._b, int(n_launches)))
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            load().heom_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
 
     def __del__(self):
         self.close()
