@@ -237,6 +237,37 @@ def time_batch(steps=20, per_launch=10):
             "graph": f"one CUDA graph per {per_launch} steps of all runs (capture + instantiate {t_capture:.2f} s)"}
 
 
+def time_serving(rates=(5.0, 20.0), n_requests=60, max_ado_steps=2e7, budget=120e9):
+    """The serving loop: Poisson arrivals of population-run requests (N in 2..24, D in 2..6, K in 0..1,
+    200..5000 steps, mixed precision, 120 GB device-memory budget).  The full mix is heavy-tailed
+    (mean ~2.5e9 ADO-RHS evaluations per request); the timed legs use a bounded sample of it (draws
+    above max_ado_steps ADOs x steps are redrawn) so that an offered rate can be sustained at all."""
+    from paper_1803_03498_gb300 import heom
+    from paper_1803_03498_gb300 import workloads as wl
+    from paper_1803_03498_gb300.serving import Server
+
+    full = wl.serving_stream(rates[0], 500)
+    hcache, rej = {}, 0
+    for r in full:
+        s = r.prop.system
+        key = (s.n_modes, s.D)
+        if key not in hcache:
+            hcache[key] = heom.Hierarchy(*key)
+        if heom.run_bytes(s, hcache[key], "fp32_mixed", 2) > budget:
+            rej += 1
+    del hcache
+    legs = []
+    for rate in rates:
+        reqs = wl.serving_stream(rate, n_requests, max_ado_steps=max_ado_steps)
+        st = Server(budget_bytes=budget, quantum=100, max_active=64).serve(reqs, real_time=True)
+        s = st.summary()
+        s["offered_rate_req_per_s"] = rate
+        legs.append(s)
+    return {"workload": f"Poisson arrivals, N 2..24, D 2..6, K 0..1, 200..5000 steps, fp32_mixed; timed legs: "
+                        f"{n_requests} requests redrawn to <= {max_ado_steps:.0e} ADOs x steps",
+            "budget_bytes": budget, "full_mix_rejected_fraction": rej / len(full), "legs": legs}
+
+
 def cpu_baseline(prop, seconds=12.0, seed=1):
     """The CPU oracle (single thread, as it stands) on a bounded sample of the same workload: the
     right-hand side of randomly chosen ADOs of the full hierarchy, on a random dense state."""
@@ -308,6 +339,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 variant (0: steps/20)")
     ap.add_argument("--depth", type=int, default=0, help="override the hierarchy depth (profiling cases)")
     ap.add_argument("--only", default="", choices=["", "mixed", "fp64"],
@@ -402,6 +434,8 @@ def main():
         }
         if not args.no_batch:
             line["batch"] = time_batch()
+        if not args.no_serving and ws == 1:
+            line["serving"] = time_serving()
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prop)
         print(json.dumps(line), flush=True)

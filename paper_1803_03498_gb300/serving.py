@@ -1,0 +1,199 @@
+"""Continuous-batching server for HEOM propagation requests on one GPU (host-side scheduler over the
+C ABI; every step of every propagation runs in libheom's kernels).
+
+A request is one propagation (system, rho(0), dt, steps).  The server
+  * admits arrived requests first-fit while their device workspace (heom_run_bytes) fits the remaining
+    memory budget; a request larger than the whole budget is rejected at once (it can never run);
+  * gives every admitted request its own CUDA stream and advances it by `quantum` RK4 steps at a time
+    (one replay of a CUDA graph captured at admission, so a quantum costs one launch on the host), so
+    the work of all admitted requests overlaps on the device, and requests that arrive while others
+    are running are admitted as soon as memory frees up (no batch boundary: continuous batching);
+  * on completion copies the observables back, frees the workspace and records the latency
+    (completion - arrival, wall clock).
+Results of a request do not depend on what else runs: each run uses its own workspace and the kernels
+are deterministic.  The paper runs independent propagations side by side (rotational averages,
+polarisation sequences; section "Distributed memory HEOM implementation"); this is that, served.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival_s: float
+    admitted_s: float = float("nan")
+    done_s: float = float("nan")
+    rejected: bool = False
+    reason: str = ""
+    n_ado: int = 0
+    n_steps: int = 0
+    workspace_bytes: int = 0
+    observables: np.ndarray | None = None
+    sigma0: np.ndarray | None = None
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.arrival_s
+
+
+@dataclass
+class _Active:
+    req: object
+    run: object
+    stream: object
+    event: object
+    remaining: int
+    result: Result
+    nbytes: int
+    graph: object = None
+
+
+@dataclass
+class ServeStats:
+    results: list = field(default_factory=list)
+    wall_s: float = 0.0
+
+    def completed(self):
+        return [r for r in self.results if not r.rejected and not np.isnan(r.done_s)]
+
+    def summary(self) -> dict:
+        done = self.completed()
+        lat = np.array([r.latency_s for r in done]) if done else np.array([np.nan])
+        evals = sum(r.n_ado * 4 * r.n_steps for r in done)
+        return {
+            "requests": len(self.results),
+            "completed": len(done),
+            "rejected": sum(r.rejected for r in self.results),
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(np.mean(lat)),
+            "throughput_req_per_s": len(done) / self.wall_s if self.wall_s > 0 else 0.0,
+            "ado_rhs_evals_per_s": evals / self.wall_s if self.wall_s > 0 else 0.0,
+            "wall_s": self.wall_s,
+        }
+
+
+class Server:
+    def __init__(self, budget_bytes: float = 120e9, precision: str = "fp32_mixed", quantum: int = 100,
+                 max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False):
+        if obs_stride > 0 and quantum % obs_stride:
+            raise ValueError("obs_stride must divide quantum")
+        self.budget = int(budget_bytes)
+        self.precision = precision
+        self.quantum = int(quantum)
+        self.max_active = int(max_active)
+        self.obs_stride = int(obs_stride)
+        self.keep_sigma0 = keep_sigma0
+        self._hier_cache = {}
+
+    def _hier(self, heom, M, D):
+        key = (M, D)
+        if key not in self._hier_cache:
+            self._hier_cache[key] = heom.Hierarchy(M, D)
+        return self._hier_cache[key]
+
+    def serve(self, requests, real_time: bool = True) -> ServeStats:
+        """Serve `requests` (workloads.Request: arrival_s, prop, rid) and return per-request results.
+        With real_time the arrivals follow the wall clock; otherwise all requests arrive at t = 0."""
+        import torch
+
+        from . import heom
+
+        heom.load()
+        reqs = sorted(requests, key=lambda r: r.arrival_s)
+        arrivals = deque(reqs)
+        pending: deque = deque()
+        active: list[_Active] = []
+        results: dict[int, Result] = {}
+        used = 0
+        streams = [torch.cuda.Stream() for _ in range(self.max_active)]
+        free_streams = list(range(self.max_active))
+        t0 = time.perf_counter()
+
+        def now():
+            return time.perf_counter() - t0
+
+        while arrivals or pending or active:
+            t = now()
+            while arrivals and (not real_time or arrivals[0].arrival_s <= t):
+                r = arrivals.popleft()
+                res = Result(r.rid, r.arrival_s if real_time else 0.0, n_ado=r.prop.system.n_ado,
+                             n_steps=r.prop.n_steps)
+                results[r.rid] = res
+                s = r.prop.system
+                hier = self._hier(heom, s.n_modes, s.D)
+                mr = (r.prop.n_steps // self.obs_stride + 2) if self.obs_stride > 0 else 2
+                try:
+                    res.workspace_bytes = heom.run_bytes(s, hier, self.precision, mr)
+                except heom.HeomError as e:
+                    res.rejected, res.reason = True, str(e)
+                    continue
+                if res.workspace_bytes > self.budget:
+                    res.rejected, res.reason = True, "workspace above the device-memory budget"
+                    continue
+                pending.append((r, hier, mr))
+            # admission: first fit in arrival order
+            i = 0
+            while i < len(pending) and free_streams:
+                r, hier, mr = pending[i]
+                res = results[r.rid]
+                if used + res.workspace_bytes <= self.budget:
+                    del pending[i]
+                    si = free_streams.pop()
+                    st = streams[si]
+                    with torch.cuda.stream(st):
+                        run = heom.Run(r.prop.system, r.prop.rho0_re, r.prop.rho0_im, precision=self.precision,
+                                       w=r.prop.w, max_records=mr, hier=hier, stream=st)
+                    used += res.workspace_bytes
+                    res.admitted_s = now()
+                    graph = None
+                    if r.prop.n_steps >= self.quantum:
+                        graph = heom.Batch([run], r.prop.dt_fs, self.quantum, self.obs_stride)
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                    active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph))
+                else:
+                    i += 1
+            # progress: finished quanta get the next quantum or complete
+            progressed = False
+            for a in list(active):
+                if not a.event.query():
+                    continue
+                progressed = True
+                if a.remaining > 0:
+                    st = streams[a.stream]
+                    if a.graph is not None and a.remaining >= self.quantum:
+                        a.graph.launch(1)
+                        q = self.quantum
+                    else:
+                        q = a.remaining
+                        a.run.propagate(a.req.prop.dt_fs, q, self.obs_stride)
+                    a.remaining -= q
+                    a.event = torch.cuda.Event()
+                    a.event.record(st)
+                else:
+                    res = a.result
+                    res.observables = a.run.observables()
+                    if self.keep_sigma0:
+                        res.sigma0 = a.run.sigma0()
+                    res.done_s = now()
+                    if a.graph is not None:
+                        a.graph.close()
+                    a.run.close()
+                    a.run = None
+                    used -= a.nbytes
+                    free_streams.append(a.stream)
+                    active.remove(a)
+            if not progressed:
+                if arrivals and real_time and not active and not pending:
+                    time.sleep(max(0.0, min(arrivals[0].arrival_s - now(), 0.01)))
+                else:
+                    time.sleep(0.0002)
+        stats = ServeStats(results=[results[k] for k in sorted(results)], wall_s=now())
+        return stats

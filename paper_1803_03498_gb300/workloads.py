@@ -168,17 +168,22 @@ class Request:
 
 
 def serving_stream(rate_per_s: float, n_requests: int, seed: int = 1803005, dt_fs: float = 0.5,
-                   n_max: int = 24, d_max: int = 6, steps_lo: int = 200, steps_hi: int = 5000):
-    """Poisson arrivals; population runs from |1><1| of random systems."""
+                   n_max: int = 24, d_max: int = 6, steps_lo: int = 200, steps_hi: int = 5000,
+                   max_ado_steps: float | None = None):
+    """Poisson arrivals; population runs from |1><1| of random systems.  With max_ado_steps, draws
+    whose ADO count times step count exceeds it are redrawn (a bounded sample of the same mix)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     for r in range(n_requests):
         t += rng.exponential(1.0 / rate_per_s)
-        n = int(rng.integers(2, n_max + 1))
-        D = int(rng.integers(2, d_max + 1))
-        K = int(rng.integers(0, 2))
-        steps = int(rng.integers(steps_lo, steps_hi + 1))
+        while True:
+            n = int(rng.integers(2, n_max + 1))
+            D = int(rng.integers(2, d_max + 1))
+            K = int(rng.integers(0, 2))
+            steps = int(rng.integers(steps_lo, steps_hi + 1))
+            if max_ado_steps is None or comb(n * (K + 1) + D, D) * steps <= max_ado_steps:
+                break
         sysm = _random_system(rng, n, D, K, f"req{r} N={n} K={K} D={D}")
         re, im = _pure(n, 0)
         out.append(Request(t, Propagation(sysm, re, im, dt_fs, steps, tag=f"req{r}"), rid=r))
