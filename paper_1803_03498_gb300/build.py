@@ -12,8 +12,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+CSRC = os.environ.get("HEOM_CSRC_DIR") or os.path.join(HERE, "csrc")
+OUT = os.environ.get("HEOM_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libheom.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hierarchy.cpp", "heom_abi.cu", "heom_static.cu"] + [f"stage_{p}_{g}.cu" for p in ("fp64", "fp32", "head") for g in "abcd"]
@@ -28,8 +28,10 @@ def _nvcc():
 
 
 def _flags():
+    extra = os.environ.get("HEOM_NVCC_DEFINES", "").split()  # e.g. -DHEOM_STAGE_WARPS=8 (tuning builds)
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                   "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
+                   "-I", os.path.join(ROOT, "include"), "-I", os.path.join(HERE, "csrc"),
+                   "--expt-relaxed-constexpr"] + extra
 
 
 def _stale(obj, deps):

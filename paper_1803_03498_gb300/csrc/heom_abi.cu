@@ -381,11 +381,18 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     return HEOM_E_NOMEM;
   }
   int64_t nlink = 0;
+  struct Pending {
+    int v, s;
+    double re, im;
+  };
+  std::vector<Pending> pend;
+  pend.reserve(2 * (size_t)M);
   for (int64_t u = 0; u < h.n; ++u) {
     loff[u] = nlink;
     double g = 0;
     for (int l = 0; l < M; ++l) g += h.tuples[(size_t)u * M + l] * gam[l];
     gs[u] = g;
+    pend.clear();
     for (int l = 0; l < M; ++l) {
       const int nl = h.tuples[(size_t)u * M + l];
       for (int dir = 0; dir < 2; ++dir) {
@@ -400,15 +407,22 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
           re = f * lnu[l];
           im = f * cc[l];
         }
-        if (u < r->u_split) {
-          rh.push_back(LinkRec<double>{v, mstate[l], 0, 0, re, im});
-        } else if (body_fp64) {
-          rbd.push_back(LinkRec<double>{v, mstate[l], 0, 0, re, im});
-        } else {
-          rbf.push_back(LinkRec<float>{v, mstate[l], (float)re, (float)im});
-        }
-        ++nlink;
+        pend.push_back(Pending{v, mstate[l], re, im});
       }
+    }
+    // records of one ADO ordered by state (the kernels give all records of a state to one lane);
+    // the state field also carries u mod 32 in bits 8..12 (see LinkRec)
+    std::stable_sort(pend.begin(), pend.end(), [](const Pending &x, const Pending &y) { return x.s < y.s; });
+    const int tag = (int)(u & 31) << 8;
+    for (const Pending &q : pend) {
+      if (u < r->u_split) {
+        rh.push_back(LinkRec<double>{q.v, q.s | tag, 0, 0, q.re, q.im});
+      } else if (body_fp64) {
+        rbd.push_back(LinkRec<double>{q.v, q.s | tag, 0, 0, q.re, q.im});
+      } else {
+        rbf.push_back(LinkRec<float>{q.v, q.s | tag, (float)q.re, (float)q.im});
+      }
+      ++nlink;
     }
   }
   loff[h.n] = nlink;

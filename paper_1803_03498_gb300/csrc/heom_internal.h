@@ -11,7 +11,10 @@
 namespace heom {
 
 constexpr int kMaxStates = 24;
-constexpr int kStageWarps = 4;  // warps per CTA of the stage kernel
+#ifndef HEOM_STAGE_WARPS
+#define HEOM_STAGE_WARPS 2
+#endif
+constexpr int kStageWarps = HEOM_STAGE_WARPS;  // warps per CTA of the stage kernel
 
 void set_error(const std::string &msg);
 
@@ -21,6 +24,10 @@ void set_error(const std::string &msg);
 //   up link (v = n + e_l):    R = i s+_l(n_l)            (s+ = sqrt((n_l + 1) |c_l|), or 1)
 //   down link (v = n - e_l):  R = s-_l(n_l) (lamnu_l + i c_l)   (s- = sqrt(n_l / |c_l|), or n_l)
 // (V^x contributes +1 on row s and -1 on column s, V^o +1 on both, 2 on the diagonal).
+// The records of one ADO are ordered by s.  Field s holds the state in bits 0..7 and the owning
+// ADO's index u mod 32 in bits 8..12, so that a warp working on ADOs u0 .. u0 + 31 finds the owner
+// of a record as ((s >> 8) - u0) mod 32 without a search.
+constexpr int kRecStateMask = 0xff;
 template <typename T>
 struct LinkRec;
 template <>

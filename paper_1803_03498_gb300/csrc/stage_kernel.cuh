@@ -21,7 +21,8 @@
 //    the unrolled loops with compile-time offsets), decay and terminator;
 //  - the lanes add the link contributions to elements (s, i) and (i, s) of their ADO's output, and
 //    y + ch * output leaves with 16-byte coalesced stores.
-// A chunk with more links than kRecCap handles the rest in further synchronous batches.
+// A chunk with more links than fit the slice buffer (kRecCap slices of 2N elements, or 2 kRecCap
+// row-only slices of N elements for Hermitian runs) handles the rest in further synchronous batches.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -62,7 +63,17 @@ __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int byte
   for (int o = lane * 16; o < bytes; o += 32 * 16) cp_async16(d + o, s + o);
 }
 
-constexpr int kRecCap = 16;  // link records (and gathered slices) per warp and batch
+#ifndef HEOM_REC_CAP
+#define HEOM_REC_CAP 16
+#endif
+#ifndef HEOM_MIN_BLOCKS_FP32
+#define HEOM_MIN_BLOCKS_FP32 1
+#endif
+#ifndef HEOM_Y_SMEM
+#define HEOM_Y_SMEM 1
+#endif
+constexpr int kRecCap = HEOM_REC_CAP;  // link records (and gathered slices) per warp and batch
+constexpr bool kYSmem = HEOM_Y_SMEM != 0;  // stage y tiles through shared memory
 
 template <int N, typename CT, typename BT>
 struct StageShape {
@@ -74,6 +85,8 @@ struct StageShape {
   static constexpr int EpOwn = kOwnHead ? E : EpBody;
   static constexpr bool kRowRegs = N <= 16;                                // H row in registers
   static constexpr bool kPairs = sizeof(CT) == 4 && (N % 2) == 0;          // 16-byte tile row loads
+  // FP32 kernels with the row in registers add the links there, one lane per (ADO, state)
+  static constexpr bool kOwnerLinks = sizeof(CT) == 4 && kRowRegs;
 };
 
 // Per-warp shared-memory layout (byte offsets).
@@ -82,14 +95,15 @@ struct WarpSmem {
   using S = StageShape<N, CT, BT>;
   static constexpr int c2 = 2 * (int)sizeof(CT);
   static constexpr int tile_bytes = (S::A * S::EpOwn * c2 + 15) & ~15;
-  static constexpr int rec_bytes = kRecCap * (int)sizeof(LinkRec<CT>);
+  static constexpr int rec_bytes = 2 * kRecCap * (int)sizeof(LinkRec<CT>);  // Hermitian runs take 2 kRecCap
   static constexpr int tile0 = 0;
   static constexpr int tile1 = tile0 + tile_bytes;
   static constexpr int ybuf = tile1 + tile_bytes;
-  static constexpr int rec0 = ybuf + tile_bytes;
+  static constexpr int rec0 = ybuf + (kYSmem ? tile_bytes : 0);
   static constexpr int rec1 = rec0 + rec_bytes;
   static constexpr int gbuf = rec1 + rec_bytes;
-  static constexpr int total = gbuf + ((kRecCap * 2 * N * c2 + 15) & ~15);
+  static constexpr int tb = gbuf + ((kRecCap * 2 * N * c2 + 15) & ~15);  // owner table, 64 bytes
+  static constexpr int total = tb + 64;
 };
 
 template <int N, typename CT, typename BT>
@@ -100,49 +114,131 @@ __device__ __forceinline__ void issue_tiles(const typename Cplx<CT>::type *src_r
   warp_copy16(dst, src_region + (int64_t)(u0 - own0) * S::EpOwn, cnt * S::EpOwn * (int)sizeof(C2), lane);
 }
 
-// Gathers row s and column s of the neighbours of nrec link records into gbuf:
-// [slot][0..N) = v_{s, 0..N-1}, [slot][N..2N) = v_{0..N-1, s} (row only for Hermitian ADOs).
-// Same-precision elements go by cp.async (one group is committed); elements of the other precision
-// region are converted.
-template <int N, typename CT, typename BT>
-__device__ __forceinline__ void issue_gathers(const StageCommon &c, const LinkRec<CT> *rec, int nrec,
-                                              typename Cplx<CT>::type *gbuf, int lane) {
+// Copies W consecutive elements of neighbour v, from element e of its tile, to dst.  Elements of
+// the same precision go by cp.async (W * element size = 8 or 16 bytes); elements of the other
+// precision region are converted.
+template <int N, typename CT, typename BT, int W>
+__device__ __forceinline__ void gather_piece(const StageCommon &c, int v, int e, typename Cplx<CT>::type *dst) {
   using S = StageShape<N, CT, BT>;
   using C2 = typename Cplx<CT>::type;
   using B2 = typename Cplx<BT>::type;
-  const B2 *zb = reinterpret_cast<const B2 *>(c.zin.body);
-  const int per = c.herm ? N : 2 * N;  // Hermitian ADOs: column s is conj(row s)
-  for (int t0 = lane; t0 < nrec * per; t0 += 32) {
-    const int sl = t0 / per, el = t0 - sl * per;
-    const int t = sl * 2 * N + el;
-    const int s = rec[sl].s, v = rec[sl].v;
-    const int e = (el < N) ? (s * N + el) : ((el - N) * N + s);
-    if (v >= c.u_split) {
-      const B2 *p = zb + (int64_t)(v - c.u_split) * S::EpBody + e;
-      if constexpr (sizeof(B2) == sizeof(C2)) {
-        if constexpr (sizeof(C2) == 16) cp_async16(gbuf + t, p);
-        else cp_async8(gbuf + t, p);
-      } else {  // FP32 body read by the FP64 head kernel
-        const B2 bv = *p;
-        C2 w;
-        w.x = (CT)bv.x;
-        w.y = (CT)bv.y;
-        gbuf[t] = w;
+  if (v >= c.u_split) {
+    const B2 *p = reinterpret_cast<const B2 *>(c.zin.body) + (int64_t)(v - c.u_split) * S::EpBody + e;
+    if constexpr (sizeof(B2) == sizeof(C2)) {
+      if constexpr (W * sizeof(C2) == 16) cp_async16(dst, p);
+      else cp_async8(dst, p);
+    } else {  // FP32 body read by the FP64 head kernel
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const B2 bv = p[w];
+        C2 x;
+        x.x = (CT)bv.x;
+        x.y = (CT)bv.y;
+        dst[w] = x;
       }
-    } else {
-      const double2 *p = c.zin.head + (int64_t)v * S::E + e;
-      if constexpr (sizeof(C2) == 16) {
-        cp_async16(gbuf + t, p);
-      } else {  // FP64 head read by the FP32 body kernel
-        const double2 d = *p;
-        C2 w;
-        w.x = (CT)d.x;
-        w.y = (CT)d.y;
-        gbuf[t] = w;
+    }
+  } else {
+    const double2 *p = c.zin.head + (int64_t)v * S::E + e;
+    if constexpr (sizeof(C2) == 16) {
+      cp_async16(dst, p);
+    } else {  // FP64 head read by the FP32 body kernel
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const double2 d = p[w];
+        C2 x;
+        x.x = (CT)d.x;
+        x.y = (CT)d.y;
+        dst[w] = x;
       }
     }
   }
+}
+
+// Gathers row s -- and, for non-Hermitian runs, column s -- of the neighbours of nrec link records
+// into gbuf: slot sl holds v_{s, 0..N-1} at gbuf[sl * pitch] followed (non-Hermitian) by
+// v_{0..N-1, s}; pitch N for Hermitian runs (column s is conj(row s)), 2N otherwise.  Rows move in
+// 16-byte pieces (two FP32 elements when N is even).  One cp.async group is committed.
+template <int N, typename CT, typename BT>
+__device__ __forceinline__ void issue_gathers(const StageCommon &c, const LinkRec<CT> *rec, int nrec,
+                                              typename Cplx<CT>::type *gbuf, int lane) {
+  constexpr int PW = (sizeof(CT) == 4 && N % 2 == 0) ? 2 : 1;  // elements per row piece
+  constexpr int P = N / PW;                                     // row pieces
+  if (c.herm) {
+    for (int t0 = lane; t0 < nrec * P; t0 += 32) {
+      const int sl = t0 / P, pc = t0 - sl * P;
+      const int s = rec[sl].s & kRecStateMask;
+      gather_piece<N, CT, BT, PW>(c, rec[sl].v, s * N + pc * PW, gbuf + sl * N + pc * PW);
+    }
+  } else {
+    constexpr int per = P + N;
+    for (int t0 = lane; t0 < nrec * per; t0 += 32) {
+      const int sl = t0 / per, el = t0 - sl * per;
+      const int s = rec[sl].s & kRecStateMask;
+      if (el < P) gather_piece<N, CT, BT, PW>(c, rec[sl].v, s * N + el * PW, gbuf + sl * 2 * N + el * PW);
+      else gather_piece<N, CT, BT, 1>(c, rec[sl].v, (el - P) * N + s, gbuf + sl * 2 * N + N + (el - P));
+    }
+  }
   cp_async_commit();
+}
+
+// Link contributions by owner lane, for the FP32 kernels that keep row li of the result in
+// registers.  Every record of the window rec[0 .. nrec) belongs to lane (a, s): a = its ADO's place
+// in the chunk starting at u0, s its state.  That lane adds R v_{s, .} to its row accumulator
+// (rr, ri) and, for non-Hermitian runs, conj(R) v_{., s} to (yr, yi), which holds column s of the
+// output transposed.  The records of one ADO are ordered by state, so a lane's records are
+// contiguous; tb (64 bytes of shared memory) carries each lane's [begin, end) from the lanes that
+// read the records.  nrec <= 32.
+template <int N, typename CT, bool HERM>
+__device__ __forceinline__ void owner_links(const LinkRec<CT> *rec, int nrec, int u0, int lane, unsigned char *tb,
+                                            const typename Cplx<CT>::type *gbuf, CT (&rr)[N], CT (&ri)[N],
+                                            CT (&yr)[N], CT (&yi)[N]) {
+  using C2 = typename Cplx<CT>::type;
+  int owner = -1;
+  if (lane < nrec) {
+    const int sw = rec[lane].s;
+    owner = (((sw >> 8) - u0) & 31) * N + (sw & kRecStateMask);
+  }
+  const int prev = __shfl_up_sync(0xffffffffu, owner, 1);
+  const int next = __shfl_down_sync(0xffffffffu, owner, 1);
+  tb[lane] = 0;
+  tb[32 + lane] = 0;
+  __syncwarp();
+  if (lane < nrec) {
+    if (lane == 0 || prev != owner) tb[owner] = (unsigned char)lane;
+    if (lane == nrec - 1 || next != owner) tb[32 + owner] = (unsigned char)(lane + 1);
+  }
+  __syncwarp();
+  const int pb = tb[lane], pe = tb[32 + lane];
+  for (int p = pb; p < pe; ++p) {
+    const CT re = rec[p].re, im = rec[p].im;
+    const C2 *g = gbuf + p * (HERM ? N : 2 * N);
+    if constexpr (sizeof(CT) == 4 && N % 2 == 0) {
+      const float4 *g4 = reinterpret_cast<const float4 *>(g);
+#pragma unroll
+      for (int jp = 0; jp < N / 2; ++jp) {
+        const float4 v = g4[jp];
+        rr[2 * jp] = fma(re, v.x, fma(-im, v.y, rr[2 * jp]));
+        ri[2 * jp] = fma(re, v.y, fma(im, v.x, ri[2 * jp]));
+        rr[2 * jp + 1] = fma(re, v.z, fma(-im, v.w, rr[2 * jp + 1]));
+        ri[2 * jp + 1] = fma(re, v.w, fma(im, v.z, ri[2 * jp + 1]));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const C2 v = g[j];
+        rr[j] = fma(re, v.x, fma(-im, v.y, rr[j]));
+        ri[j] = fma(re, v.y, fma(im, v.x, ri[j]));
+      }
+    }
+    if constexpr (!HERM) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const C2 v = g[N + j];
+        yr[j] = fma(re, v.x, fma(im, v.y, yr[j]));
+        yi[j] = fma(re, v.y, fma(-im, v.x, yi[j]));
+      }
+    }
+  }
 }
 
 // Adds the contributions of the records [blo, blo + nrec) (record i at rec[i - blo]) to the output
@@ -161,8 +257,8 @@ __device__ __forceinline__ void apply_links(const LinkRec<CT> *rec, int64_t blo,
     if (k < my_cnt) {
       const int sl = (int)(a_lo - blo) + k;
       const LinkRec<CT> r = rec[sl];
-      const int s = r.s;
-      const C2 *gv = gbuf + sl * 2 * N;
+      const int s = r.s & kRecStateMask;
+      const C2 *gv = gbuf + sl * (herm ? N : 2 * N);
       if (li == s) {
         const C2 v = gv[s];
         C2 o = ot[s * N + s];
@@ -199,6 +295,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
   using C2 = typename Cplx<CT>::type;
   using R = LinkRec<CT>;
   constexpr int A = S::A, EPO = S::EpOwn;
+  constexpr bool kOwn = S::kOwnerLinks && !CPLX;  // complex H keeps the shared-memory link path
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StageCommon &c = a.c;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -234,6 +331,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
   const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
   const int nwarps = gridDim.x * kStageWarps;
   const int first = blockIdx.x * kStageWarps + warp;
+  const int cap = c.herm ? 2 * kRecCap : kRecCap;  // link records per batch (slice buffer: 2 N kRecCap)
   // lane a <= cnt of a chunk holds link_off[u0 + a]
   auto load_offs = [&](int chn) -> int64_t {
     if (chn >= n_chunks) return 0;
@@ -248,7 +346,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
     const int cnt = min(A, c.u_end - u0);
     issue_tiles<N, CT, BT>(zin_own, own0, u0, cnt, wb + W::tile0, lane);
     const int64_t lo = __shfl_sync(0xffffffffu, off_cur, 0), hi = __shfl_sync(0xffffffffu, off_cur, cnt);
-    const int nr = (int)min(hi - lo, (int64_t)kRecCap);
+    const int nr = (int)min(hi - lo, (int64_t)cap);
     warp_copy16(wb + W::rec0, recs + (lo - rbase), nr * (int)sizeof(R), lane);
     cp_async_commit();
   }
@@ -266,11 +364,11 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
       const int vcnt = min(A, c.u_end - v0);
       issue_tiles<N, CT, BT>(zin_own, own0, v0, vcnt, wb + (b ? W::tile0 : W::tile1), lane);
       const int64_t lo = __shfl_sync(0xffffffffu, off_nxt, 0), hi = __shfl_sync(0xffffffffu, off_nxt, vcnt);
-      const int nr = (int)min(hi - lo, (int64_t)kRecCap);
+      const int nr = (int)min(hi - lo, (int64_t)cap);
       warp_copy16(wb + (b ? W::rec0 : W::rec1), recs + (lo - rbase), nr * (int)sizeof(R), lane);
     }
     cp_async_commit();
-    if (has_y) issue_tiles<N, CT, BT>(y_own, own0, u0, cnt, ybuf, lane);
+    if (kYSmem && has_y) issue_tiles<N, CT, BT>(y_own, own0, u0, cnt, ybuf, lane);
     cp_async_commit();
     cp_async_wait<2>();  // this chunk's tiles and first records have landed
     __syncwarp();
@@ -279,13 +377,13 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
     const bool active = lane_ok && la < cnt;
     const int64_t my_lo = __shfl_sync(0xffffffffu, off_cur, min(la, A));
     const int64_t my_hi = __shfl_sync(0xffffffffu, off_cur, min(la + 1, A));
-    const int nrec = (int)min(hi - lo, (int64_t)kRecCap);
+    const int nrec = (int)min(hi - lo, (int64_t)cap);
     issue_gathers<N, CT, BT>(c, rec, nrec, gbuf, lane);
 
+    const bool herm = c.herm != 0;
+    CT rr[N], ri[N];  // row li of the result: real and imaginary parts
     {  // commutator -i (H s - s H), decay and terminator of row li
       const C2 *zt = zt_all + la * EPO;
-      const bool herm = c.herm != 0;
-      CT rr[N], ri[N];  // row li of -i (H s - s H): real and imaginary parts
       C2 zr[N];         // own row s_{li, .}
       if (active) {
 #pragma unroll
@@ -354,7 +452,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
           }
         }
       }
-      if (herm) {
+      if (herm && !kOwn) {
         // s and H Hermitian: s H = (H s)^dagger, so -i (H s - s H)_ij = -i (P_ij - conj(P_ji)) with
         // P = H s; in the (rr, ri) = -i P form that is (rr_ij + rr_ji, ri_ij - ri_ji).
         __syncwarp();  // every lane is done reading the tile
@@ -379,16 +477,82 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
       }
       if (active) {  // decay and terminator
         const CT gsv = (CT)c.gsum[u0 + la];
+        // Hermitian runs on the owner path add Q + Q^dagger at the end: half the rate here
+        const CT hf = (kOwn && herm) ? (CT)0.5 : (CT)1;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           CT f;
           if constexpr (kTsum) f = gsv + tsum[kTsum ? j : 0];
           else f = gsv + ((j != li) ? (term_i + a.term[j]) : (CT)0);
+          if constexpr (kOwn) f *= hf;
           rr[j] = fma(-f, zr[j].x, rr[j]);
           ri[j] = fma(-f, zr[j].y, ri[j]);
         }
       }
-      __syncwarp();  // every lane is done reading the tile: it becomes the output buffer
+      if constexpr (!kOwn) {
+        __syncwarp();  // every lane is done reading the tile: it becomes the output buffer
+        if (active) {
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            C2 w;
+            w.x = rr[j];
+            w.y = ri[j];
+            zt_all[la * EPO + li * N + j] = w;
+          }
+        }
+      }
+    }
+    cp_async_wait<0>();  // gathers, y and the next chunk's copies have landed
+    __syncwarp();
+    if constexpr (kOwn) {
+      // Row li of Q in (rr, ri): -i H s (Hermitian) or -i (H s - s H), the decay, and R v_{li, .} of
+      // the records of state li.  Non-Hermitian runs collect conj(R) v_{., li} in (yr, yi).
+      unsigned char *tb = wb + W::tb;
+      CT yr[N], yi[N];
+      if (!herm) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          yr[j] = 0;
+          yi[j] = 0;
+        }
+      }
+      if (herm) owner_links<N, CT, true>(rec, nrec, u0, lane, tb, gbuf, rr, ri, yr, yi);
+      else owner_links<N, CT, false>(rec, nrec, u0, lane, tb, gbuf, rr, ri, yr, yi);
+      for (int64_t blo = lo + nrec; blo < hi; blo += cap) {  // further link batches
+        __syncwarp();
+        const int nr = (int)min(hi - blo, (int64_t)cap);
+        warp_copy16(rec, recs + (blo - rbase), nr * (int)sizeof(R), lane);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        issue_gathers<N, CT, BT>(c, rec, nr, gbuf, lane);
+        cp_async_wait<0>();
+        __syncwarp();
+        if (herm) owner_links<N, CT, true>(rec, nr, u0, lane, tb, gbuf, rr, ri, yr, yi);
+        else owner_links<N, CT, false>(rec, nr, u0, lane, tb, gbuf, rr, ri, yr, yi);
+      }
+      // result_ij = Q_ij + conj(Q_ji) (Hermitian) or Q_ij + (yr, yi) of lane j at i, through the tile
+      // (every lane is done reading it: the waits above end with __syncwarp)
+      if (active) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          C2 w;
+          w.x = herm ? rr[j] : yr[j];
+          w.y = herm ? ri[j] : yi[j];
+          zt_all[la * EPO + li * N + j] = w;
+        }
+      }
+      __syncwarp();
+      if (active) {
+        const CT sg = herm ? (CT)-1 : (CT)1;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const C2 t = zt_all[la * EPO + j * N + li];
+          rr[j] += t.x;
+          ri[j] = fma(sg, t.y, ri[j]);
+        }
+      }
+      __syncwarp();
       if (active) {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
@@ -398,22 +562,21 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
           zt_all[la * EPO + li * N + j] = w;
         }
       }
-    }
-    cp_async_wait<0>();  // gathers, y and the next chunk's copies have landed
-    __syncwarp();
-    C2 *ot = zt_all + la * EPO;
-    apply_links<N, CT, BT>(rec, lo, nrec, my_lo, my_hi, active, li, c.herm != 0, ot, gbuf);
-    for (int64_t blo = lo + nrec; blo < hi; blo += kRecCap) {  // further link batches
-      __syncwarp();
-      const int nr = (int)min(hi - blo, (int64_t)kRecCap);
-      warp_copy16(rec, recs + (blo - rbase), nr * (int)sizeof(R), lane);
-      cp_async_commit();
-      cp_async_wait<0>();
-      __syncwarp();
-      issue_gathers<N, CT, BT>(c, rec, nr, gbuf, lane);
-      cp_async_wait<0>();
-      __syncwarp();
-      apply_links<N, CT, BT>(rec, blo, nr, my_lo, my_hi, active, li, c.herm != 0, ot, gbuf);
+    } else {
+      C2 *ot = zt_all + la * EPO;
+      apply_links<N, CT, BT>(rec, lo, nrec, my_lo, my_hi, active, li, herm, ot, gbuf);
+      for (int64_t blo = lo + nrec; blo < hi; blo += cap) {  // further link batches
+        __syncwarp();
+        const int nr = (int)min(hi - blo, (int64_t)cap);
+        warp_copy16(rec, recs + (blo - rbase), nr * (int)sizeof(R), lane);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        issue_gathers<N, CT, BT>(c, rec, nr, gbuf, lane);
+        cp_async_wait<0>();
+        __syncwarp();
+        apply_links<N, CT, BT>(rec, blo, nr, my_lo, my_hi, active, li, herm, ot, gbuf);
+      }
     }
     __syncwarp();
     // y + ch * rhs over the chunk's contiguous tiles, 16 bytes per access
@@ -421,7 +584,8 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
       C2 *dst = out_own + (int64_t)(u0 - own0) * EPO;
       if constexpr (sizeof(CT) == 4) {
         const float4 *o4 = reinterpret_cast<const float4 *>(zt_all);
-        const float4 *y4 = reinterpret_cast<const float4 *>(ybuf);
+        const float4 *y4 = kYSmem ? reinterpret_cast<const float4 *>(ybuf)
+                                  : reinterpret_cast<const float4 *>(y_own + (int64_t)(u0 - own0) * EPO);
         float4 *d4 = reinterpret_cast<float4 *>(dst);
         const float chv = (float)a.ch;
         for (int t = lane; t < cnt * EPO / 2; t += 32) {
@@ -444,7 +608,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
         for (int t = lane; t < cnt * EPO; t += 32) {
           C2 w = zt_all[t];
           if (has_y) {
-            const C2 yv = ybuf[t];
+            const C2 yv = kYSmem ? ybuf[t] : y_own[(int64_t)(u0 - own0) * EPO + t];
             w.x = fma(a.ch, w.x, yv.x);
             w.y = fma(a.ch, w.y, yv.y);
           } else {
