@@ -64,7 +64,7 @@ __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int byte
 }
 
 #ifndef HEOM_REC_CAP
-#define HEOM_REC_CAP 16
+#define HEOM_REC_CAP 32
 #endif
 #ifndef HEOM_MIN_BLOCKS_FP32
 #define HEOM_MIN_BLOCKS_FP32 1
@@ -187,25 +187,37 @@ __device__ __forceinline__ void issue_gathers(const StageCommon &c, const LinkRe
 // (rr, ri) and, for non-Hermitian runs, conj(R) v_{., s} to (yr, yi), which holds column s of the
 // output transposed.  The records of one ADO are ordered by state, so a lane's records are
 // contiguous; tb (64 bytes of shared memory) carries each lane's [begin, end) from the lanes that
-// read the records.  nrec <= 32.
+// read the records, 32 records per round.  nrec <= 2 kRecCap <= 255.
 template <int N, typename CT, bool HERM>
 __device__ __forceinline__ void owner_links(const LinkRec<CT> *rec, int nrec, int u0, int lane, unsigned char *tb,
                                             const typename Cplx<CT>::type *gbuf, CT (&rr)[N], CT (&ri)[N],
                                             CT (&yr)[N], CT (&yi)[N]) {
   using C2 = typename Cplx<CT>::type;
-  int owner = -1;
-  if (lane < nrec) {
-    const int sw = rec[lane].s;
-    owner = (((sw >> 8) - u0) & 31) * N + (sw & kRecStateMask);
-  }
-  const int prev = __shfl_up_sync(0xffffffffu, owner, 1);
-  const int next = __shfl_down_sync(0xffffffffu, owner, 1);
+  constexpr int kRounds = (2 * kRecCap + 31) / 32;
+  auto owner_of = [&](int t) -> int {
+    if (t >= nrec) return -1;
+    const int sw = rec[t].s;
+    return (((sw >> 8) - u0) & 31) * N + (sw & kRecStateMask);
+  };
   tb[lane] = 0;
   tb[32 + lane] = 0;
   __syncwarp();
-  if (lane < nrec) {
-    if (lane == 0 || prev != owner) tb[owner] = (unsigned char)lane;
-    if (lane == nrec - 1 || next != owner) tb[32 + owner] = (unsigned char)(lane + 1);
+  int own = owner_of(lane);
+  int before = -1;  // owner of record 32 r - 1
+  for (int r = 0; r < kRounds && 32 * r < nrec; ++r) {
+    const int t = 32 * r + lane;
+    const int nxt_round = owner_of(t + 32);
+    int prev = __shfl_up_sync(0xffffffffu, own, 1);
+    int next = __shfl_down_sync(0xffffffffu, own, 1);
+    const int next_first = __shfl_sync(0xffffffffu, nxt_round, 0);
+    if (lane == 0) prev = before;
+    if (lane == 31) next = next_first;
+    if (t < nrec) {
+      if (prev != own) tb[own] = (unsigned char)t;
+      if (next != own) tb[32 + own] = (unsigned char)(t + 1);
+    }
+    before = __shfl_sync(0xffffffffu, own, 31);
+    own = nxt_round;
   }
   __syncwarp();
   const int pb = tb[lane], pe = tb[32 + lane];
