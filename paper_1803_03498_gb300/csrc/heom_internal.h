@@ -11,10 +11,6 @@
 namespace heom {
 
 constexpr int kMaxStates = 24;
-#ifndef HEOM_STAGE_WARPS
-#define HEOM_STAGE_WARPS 2
-#endif
-constexpr int kStageWarps = HEOM_STAGE_WARPS;  // warps per CTA of the stage kernel
 
 void set_error(const std::string &msg);
 

@@ -19,9 +19,12 @@
 //  - while those are in flight, lane (a, i) computes row i of ADO a: the commutator (the lanes of
 //    one ADO read the same tile words, a broadcast; H sits in the kernel parameters, addressed by
 //    the unrolled loops with compile-time offsets), decay and terminator;
-//  - the lanes add the link contributions to elements (s, i) and (i, s) of their ADO's output, and
-//    y + ch * output leaves with 16-byte coalesced stores.
-// A chunk with more links than fit the slice buffer (kRecCap slices of 2N elements, or 2 kRecCap
+//  - links: in Hermitian runs of the FP32 kernels with N <= 16, every link record goes to the one lane
+//    that owns row s of its ADO, which adds R v_{s, .} to its row in registers, and a transpose through
+//    shared memory forms Q + Q^dagger at the end; otherwise the lanes add each link to elements (s, i)
+//    and (i, s) of their ADO's output tile in shared memory;
+//  - y + ch * output leaves with 16-byte coalesced stores.
+// A chunk with more links than fit the slice buffer (RC slices of 2N elements, or 2 RC
 // row-only slices of N elements for Hermitian runs) handles the rest in further synchronous batches.
 #pragma once
 #include <cuda_runtime.h>
@@ -63,21 +66,35 @@ __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int byte
   for (int o = lane * 16; o < bytes; o += 32 * 16) cp_async16(d + o, s + o);
 }
 
-#ifndef HEOM_REC_CAP
-#define HEOM_REC_CAP 32
+// Launch shape and buffer sizes (measured on the LHCII-like and FMO-like hierarchies; the macros
+// exist for tuning builds).  Link records per warp and batch: RC of 2N-element slices (2 RC row-only
+// slices for Hermitian runs).
+#ifndef HEOM_STAGE_WARPS
+#define HEOM_STAGE_WARPS 4  // warps per CTA, FP32 kernels
 #endif
-#ifndef HEOM_MIN_BLOCKS_FP32
-#define HEOM_MIN_BLOCKS_FP32 1
+#ifndef HEOM_STAGE_WARPS_FP64
+#define HEOM_STAGE_WARPS_FP64 2
+#endif
+#ifndef HEOM_REC_CAP
+#define HEOM_REC_CAP 16  // FP32, N > 10
+#endif
+#ifndef HEOM_REC_CAP_SMALL
+#define HEOM_REC_CAP_SMALL 32  // FP32, N <= 10 (small tiles leave room for more records)
+#endif
+#ifndef HEOM_REC_CAP_FP64
+#define HEOM_REC_CAP_FP64 32
 #endif
 #ifndef HEOM_Y_SMEM
 #define HEOM_Y_SMEM 1
 #endif
-constexpr int kRecCap = HEOM_REC_CAP;  // link records (and gathered slices) per warp and batch
 constexpr bool kYSmem = HEOM_Y_SMEM != 0;  // stage y tiles through shared memory
 
 template <int N, typename CT, typename BT>
 struct StageShape {
   static constexpr int E = N * N;
+  static constexpr int WARPS = sizeof(CT) == 8 ? HEOM_STAGE_WARPS_FP64 : HEOM_STAGE_WARPS;
+  static constexpr int RC = sizeof(CT) == 8 ? HEOM_REC_CAP_FP64 : (N <= 10 ? HEOM_REC_CAP_SMALL : HEOM_REC_CAP);
+  static_assert(2 * RC <= 255, "owner table holds record indices in bytes");
   // ADOs per warp; at most 31 so that lanes 0..A hold the A + 1 record offsets of a chunk
   static constexpr int A = (32 / N < 32) ? 32 / N : 31;
   static constexpr bool kOwnHead = sizeof(CT) == 8 && sizeof(BT) == 4;     // mixed-precision head kernel
@@ -95,14 +112,14 @@ struct WarpSmem {
   using S = StageShape<N, CT, BT>;
   static constexpr int c2 = 2 * (int)sizeof(CT);
   static constexpr int tile_bytes = (S::A * S::EpOwn * c2 + 15) & ~15;
-  static constexpr int rec_bytes = 2 * kRecCap * (int)sizeof(LinkRec<CT>);  // Hermitian runs take 2 kRecCap
+  static constexpr int rec_bytes = 2 * S::RC * (int)sizeof(LinkRec<CT>);  // Hermitian runs take 2 RC
   static constexpr int tile0 = 0;
   static constexpr int tile1 = tile0 + tile_bytes;
   static constexpr int ybuf = tile1 + tile_bytes;
   static constexpr int rec0 = ybuf + (kYSmem ? tile_bytes : 0);
   static constexpr int rec1 = rec0 + rec_bytes;
   static constexpr int gbuf = rec1 + rec_bytes;
-  static constexpr int tb = gbuf + ((kRecCap * 2 * N * c2 + 15) & ~15);  // owner table, 64 bytes
+  static constexpr int tb = gbuf + ((S::RC * 2 * N * c2 + 15) & ~15);  // owner table, 64 bytes
   static constexpr int total = tb + 64;
 };
 
@@ -181,19 +198,18 @@ __device__ __forceinline__ void issue_gathers(const StageCommon &c, const LinkRe
   cp_async_commit();
 }
 
-// Link contributions by owner lane, for the FP32 kernels that keep row li of the result in
-// registers.  Every record of the window rec[0 .. nrec) belongs to lane (a, s): a = its ADO's place
-// in the chunk starting at u0, s its state.  That lane adds R v_{s, .} to its row accumulator
-// (rr, ri) and, for non-Hermitian runs, conj(R) v_{., s} to (yr, yi), which holds column s of the
-// output transposed.  The records of one ADO are ordered by state, so a lane's records are
+// Link contributions by owner lane, for Hermitian runs of the FP32 kernels that keep row li of the
+// result in registers.  Every record of the window rec[0 .. nrec) belongs to lane (a, s): a = its
+// ADO's place in the chunk starting at u0, s its state.  That lane adds R v_{s, .} to its row
+// accumulator (rr, ri); the column part conj(R) v_{., s} follows from Q + Q^dagger at the end.
+// The records of one ADO are ordered by state, so a lane's records are
 // contiguous; tb (64 bytes of shared memory) carries each lane's [begin, end) from the lanes that
-// read the records, 32 records per round.  nrec <= 2 kRecCap <= 255.
-template <int N, typename CT, bool HERM>
+// read the records, 32 records per round.  nrec <= 2 RC <= 255.
+template <int N, typename CT>
 __device__ __forceinline__ void owner_links(const LinkRec<CT> *rec, int nrec, int u0, int lane, unsigned char *tb,
-                                            const typename Cplx<CT>::type *gbuf, CT (&rr)[N], CT (&ri)[N],
-                                            CT (&yr)[N], CT (&yi)[N]) {
+                                            const typename Cplx<CT>::type *gbuf, CT (&rr)[N], CT (&ri)[N]) {
   using C2 = typename Cplx<CT>::type;
-  constexpr int kRounds = (2 * kRecCap + 31) / 32;
+  constexpr int kRounds = (2 * StageShape<N, CT, CT>::RC + 31) / 32;
   auto owner_of = [&](int t) -> int {
     if (t >= nrec) return -1;
     const int sw = rec[t].s;
@@ -223,7 +239,7 @@ __device__ __forceinline__ void owner_links(const LinkRec<CT> *rec, int nrec, in
   const int pb = tb[lane], pe = tb[32 + lane];
   for (int p = pb; p < pe; ++p) {
     const CT re = rec[p].re, im = rec[p].im;
-    const C2 *g = gbuf + p * (HERM ? N : 2 * N);
+    const C2 *g = gbuf + p * N;
     if constexpr (sizeof(CT) == 4 && N % 2 == 0) {
       const float4 *g4 = reinterpret_cast<const float4 *>(g);
 #pragma unroll
@@ -240,14 +256,6 @@ __device__ __forceinline__ void owner_links(const LinkRec<CT> *rec, int nrec, in
         const C2 v = g[j];
         rr[j] = fma(re, v.x, fma(-im, v.y, rr[j]));
         ri[j] = fma(re, v.y, fma(im, v.x, ri[j]));
-      }
-    }
-    if constexpr (!HERM) {
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        const C2 v = g[N + j];
-        yr[j] = fma(re, v.x, fma(im, v.y, yr[j]));
-        yi[j] = fma(re, v.y, fma(-im, v.x, yi[j]));
       }
     }
   }
@@ -301,7 +309,7 @@ __device__ __forceinline__ void apply_links(const LinkRec<CT> *rec, int64_t blo,
 }
 
 template <int N, typename CT, typename BT, bool CPLX>
-__global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_constant__ StageArgs<CT> a) {
+__global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kernel(const __grid_constant__ StageArgs<CT> a) {
   using S = StageShape<N, CT, BT>;
   using W = WarpSmem<N, CT, BT>;
   using C2 = typename Cplx<CT>::type;
@@ -341,9 +349,9 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
   const int own0 = S::kOwnHead ? 0 : c.u_split;
 
   const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
-  const int nwarps = gridDim.x * kStageWarps;
-  const int first = blockIdx.x * kStageWarps + warp;
-  const int cap = c.herm ? 2 * kRecCap : kRecCap;  // link records per batch (slice buffer: 2 N kRecCap)
+  const int nwarps = gridDim.x * S::WARPS;
+  const int first = blockIdx.x * S::WARPS + warp;
+  const int cap = c.herm ? 2 * S::RC : S::RC;  // link records per batch (slice buffer: 2 N RC elements)
   // lane a <= cnt of a chunk holds link_off[u0 + a]
   auto load_offs = [&](int chn) -> int64_t {
     if (chn >= n_chunks) return 0;
@@ -393,6 +401,9 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
     issue_gathers<N, CT, BT>(c, rec, nrec, gbuf, lane);
 
     const bool herm = c.herm != 0;
+    // owner-lane links for Hermitian runs; non-Hermitian runs need row and column work per link,
+    // which the shared-memory form spreads over the lanes
+    const bool own_path = kOwn && herm;
     CT rr[N], ri[N];  // row li of the result: real and imaginary parts
     {  // commutator -i (H s - s H), decay and terminator of row li
       const C2 *zt = zt_all + la * EPO;
@@ -464,7 +475,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
           }
         }
       }
-      if (herm && !kOwn) {
+      if (herm && !own_path) {
         // s and H Hermitian: s H = (H s)^dagger, so -i (H s - s H)_ij = -i (P_ij - conj(P_ji)) with
         // P = H s; in the (rr, ri) = -i P form that is (rr_ij + rr_ji, ri_ij - ri_ji).
         __syncwarp();  // every lane is done reading the tile
@@ -489,8 +500,8 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
       }
       if (active) {  // decay and terminator
         const CT gsv = (CT)c.gsum[u0 + la];
-        // Hermitian runs on the owner path add Q + Q^dagger at the end: half the rate here
-        const CT hf = (kOwn && herm) ? (CT)0.5 : (CT)1;
+        // the owner path adds Q + Q^dagger at the end: half the rate here
+        const CT hf = own_path ? (CT)0.5 : (CT)1;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           CT f;
@@ -501,7 +512,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
           ri[j] = fma(-f, zr[j].y, ri[j]);
         }
       }
-      if constexpr (!kOwn) {
+      if (!own_path) {
         __syncwarp();  // every lane is done reading the tile: it becomes the output buffer
         if (active) {
 #pragma unroll
@@ -516,20 +527,10 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
     }
     cp_async_wait<0>();  // gathers, y and the next chunk's copies have landed
     __syncwarp();
-    if constexpr (kOwn) {
-      // Row li of Q in (rr, ri): -i H s (Hermitian) or -i (H s - s H), the decay, and R v_{li, .} of
-      // the records of state li.  Non-Hermitian runs collect conj(R) v_{., li} in (yr, yi).
+    if (own_path) {
+      // Row li of Q in (rr, ri): -i H s, half the decay, and R v_{li, .} of the records of state li
       unsigned char *tb = wb + W::tb;
-      CT yr[N], yi[N];
-      if (!herm) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          yr[j] = 0;
-          yi[j] = 0;
-        }
-      }
-      if (herm) owner_links<N, CT, true>(rec, nrec, u0, lane, tb, gbuf, rr, ri, yr, yi);
-      else owner_links<N, CT, false>(rec, nrec, u0, lane, tb, gbuf, rr, ri, yr, yi);
+      owner_links<N, CT>(rec, nrec, u0, lane, tb, gbuf, rr, ri);
       for (int64_t blo = lo + nrec; blo < hi; blo += cap) {  // further link batches
         __syncwarp();
         const int nr = (int)min(hi - blo, (int64_t)cap);
@@ -540,28 +541,26 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
         issue_gathers<N, CT, BT>(c, rec, nr, gbuf, lane);
         cp_async_wait<0>();
         __syncwarp();
-        if (herm) owner_links<N, CT, true>(rec, nr, u0, lane, tb, gbuf, rr, ri, yr, yi);
-        else owner_links<N, CT, false>(rec, nr, u0, lane, tb, gbuf, rr, ri, yr, yi);
+        owner_links<N, CT>(rec, nr, u0, lane, tb, gbuf, rr, ri);
       }
-      // result_ij = Q_ij + conj(Q_ji) (Hermitian) or Q_ij + (yr, yi) of lane j at i, through the tile
-      // (every lane is done reading it: the waits above end with __syncwarp)
+      // result_ij = Q_ij + conj(Q_ji) through the tile (every lane is done reading it: the waits above
+      // end with __syncwarp)
       if (active) {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           C2 w;
-          w.x = herm ? rr[j] : yr[j];
-          w.y = herm ? ri[j] : yi[j];
+          w.x = rr[j];
+          w.y = ri[j];
           zt_all[la * EPO + li * N + j] = w;
         }
       }
       __syncwarp();
       if (active) {
-        const CT sg = herm ? (CT)-1 : (CT)1;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           const C2 t = zt_all[la * EPO + j * N + li];
           rr[j] += t.x;
-          ri[j] = fma(sg, t.y, ri[j]);
+          ri[j] -= t.y;
         }
       }
       __syncwarp();
@@ -641,7 +640,8 @@ __global__ void __launch_bounds__(kStageWarps * 32) stage_kernel(const __grid_co
 template <int N, typename CT, typename BT, bool CPLX>
 int launch_v(const StageArgs<CT> &a, cudaStream_t st, int sm_count) {
   const StageCommon &c = a.c;
-  const size_t smem = (size_t)kStageWarps * WarpSmem<N, CT, BT>::total;
+  constexpr int WARPS = StageShape<N, CT, BT>::WARPS;
+  const size_t smem = (size_t)WARPS * WarpSmem<N, CT, BT>::total;
   static int per_sm = 0;  // occupancy of this instantiation (its shared memory size is fixed)
   if (per_sm == 0) {
     if (smem > 48 * 1024) {
@@ -654,7 +654,7 @@ int launch_v(const StageArgs<CT> &a, cudaStream_t st, int sm_count) {
     }
     int ps = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, stage_kernel<N, CT, BT, CPLX>,
-                                                                  kStageWarps * 32, smem);
+                                                                  WARPS * 32, smem);
     if (e != cudaSuccess || ps < 1) {
       set_error(std::string("stage kernel: occupancy query failed or zero blocks: ") + cudaGetErrorString(e));
       return -4;
@@ -663,9 +663,9 @@ int launch_v(const StageArgs<CT> &a, cudaStream_t st, int sm_count) {
   }
   constexpr int A = StageShape<N, CT, BT>::A;
   const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
-  const int blocks_needed = (n_chunks + kStageWarps - 1) / kStageWarps;
+  const int blocks_needed = (n_chunks + WARPS - 1) / WARPS;
   const int grid = std::max(1, std::min(blocks_needed, per_sm * sm_count));
-  stage_kernel<N, CT, BT, CPLX><<<grid, kStageWarps * 32, smem, st>>>(a);
+  stage_kernel<N, CT, BT, CPLX><<<grid, WARPS * 32, smem, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("stage kernel launch: ") + cudaGetErrorString(e));
