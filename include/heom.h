@@ -40,6 +40,12 @@ extern "C" {
 #define HEOM_FP32_MIXED 1 /* levels >= 2 stored and computed in FP32; levels 0 and 1 (the root ADO
                              sigma_0 and its direct neighbours), the RK4 combination of sigma_0 and
                              every observable reduction in FP64 */
+#define HEOM_SPLIT_TF32 2 /* storage and arithmetic as HEOM_FP32_MIXED, except that for Hermitian runs
+                             with real H and n_states <= 16 the commutator of levels >= 2 runs on the
+                             tensor cores: sigma and H are split into TF32 high and low parts and
+                             sigma H = hi*hi + lo*hi + hi*lo is accumulated in FP32 (about 21 bits).
+                             Other runs at this precision compute exactly as HEOM_FP32_MIXED.  Not in
+                             the paper (which computes in FP64). */
 
 typedef struct heom_hier heom_hier;
 typedef struct heom_run heom_run;

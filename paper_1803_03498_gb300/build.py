@@ -16,8 +16,10 @@ CSRC = os.environ.get("HEOM_CSRC_DIR") or os.path.join(HERE, "csrc")
 OUT = os.environ.get("HEOM_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libheom.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hierarchy.cpp", "heom_abi.cu", "heom_static.cu"] + [f"stage_{p}_{g}.cu" for p in ("fp64", "fp32", "head") for g in "abcd"]
-HEADERS = ["hierarchy.h", "heom_internal.h", "stage_kernel.cuh"]
+SOURCES = (["hierarchy.cpp", "heom_abi.cu", "heom_static.cu"]
+           + [f"stage_{p}_{g}.cu" for p in ("fp64", "fp32", "head") for g in "abcd"]
+           + ["stage_tc_a.cu", "stage_tc_b.cu"])
+HEADERS = ["hierarchy.h", "heom_internal.h", "stage_kernel.cuh", "stage_tc.cuh"]
 
 
 def _nvcc():

@@ -69,6 +69,7 @@ struct heom_run {
   double *records = nullptr;         // [max_records][n + 5]
   double *w_dev = nullptr;           // [n] dipole weights (zeros if none)
   int64_t *rec_count = nullptr;      // device counter of records written
+  int *err_dev = nullptr;            // device flag set by a bounded device-side wait that gave up
   int64_t max_records = 0;
   int64_t records_host = 0;          // records enqueued so far (host view)
   int64_t steps_done = 0;
@@ -164,7 +165,7 @@ int check_system(const heom_system *s, const heom_hier *h, int precision) {
       return HEOM_E_ARG;
     }
   }
-  if (precision != HEOM_FP64 && precision != HEOM_FP32_MIXED) {
+  if (precision != HEOM_FP64 && precision != HEOM_FP32_MIXED && precision != HEOM_SPLIT_TF32) {
     set_error("unknown precision");
     return HEOM_E_ARG;
   }
@@ -199,7 +200,7 @@ Layout make_layout(int n, const Hierarchy &h, int u_split, int precision, int64_
   L.off_gsum = o; o = al(o + (size_t)n_ado * sizeof(double));
   L.off_rec = o; o = al(o + (size_t)std::max<int64_t>(max_records, 1) * (n + 5) * sizeof(double));
   L.off_w = o; o = al(o + (size_t)n * sizeof(double));
-  L.off_cnt = o; o = al(o + sizeof(int64_t));
+  L.off_cnt = o; o = al(o + 2 * sizeof(int64_t));  // record counter, device error flag
   L.head_bytes = al((size_t)u_split * E * sizeof(double2));
   L.body_bytes = al((size_t)(n_ado - u_split) * *Ep * be);
   for (int c = 0; c < 3; ++c) {
@@ -457,6 +458,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   r->records = reinterpret_cast<double *>(base + L.off_rec);
   r->w_dev = reinterpret_cast<double *>(base + L.off_w);
   r->rec_count = reinterpret_cast<int64_t *>(base + L.off_cnt);
+  r->err_dev = reinterpret_cast<int *>(base + L.off_cnt + sizeof(int64_t));
   r->y = view_at(base, L, 0);
   r->zA = view_at(base, L, 1);
   r->zB = view_at(base, L, 2);
@@ -473,7 +475,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     ce = cudaMemcpyAsync(r->recs_body, rbf.data(), rbf.size() * sizeof(rbf[0]), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->gsum, gs.data(), gs.size() * sizeof(double), cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(r->w_dev, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(r->rec_count, 0, sizeof(int64_t), st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(r->rec_count, 0, 2 * sizeof(int64_t), st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(base + L.off_state[0], 0, L.head_bytes + L.body_bytes, st);
   // the host vectors are pageable, so each copy has consumed its source when cudaMemcpyAsync returns
   if (ce != cudaSuccess) { delete r; return cuda_fail("workspace upload", ce); }
@@ -517,6 +519,7 @@ static StageCommon common_for(const heom_run *r, StateView zin, StateView y, Sta
   c.n = r->n;
   c.cplx_h = r->cplx_h ? 1 : 0;
   c.herm = r->herm ? 1 : 0;
+  c.err = r->err_dev;
   return c;
 }
 
@@ -570,7 +573,12 @@ static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, dou
   c.u_end = (int)r->n_ado;
   if (c.u_end > c.u_begin) {
     if ((rc = timed_begin(r))) return rc;
-    rc = launch_stage(1, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
+    rc = 1;
+    if (r->precision == HEOM_SPLIT_TF32 && r->herm && !r->cplx_h) {  // tensor-core commutator
+      rc = launch_stage_tc_a(c, ch, r->term.data(), r->H.data(), r->stream, r->sm_count);
+      if (rc == 1) rc = launch_stage_tc_b(c, ch, r->term.data(), r->H.data(), r->stream, r->sm_count);
+    }
+    if (rc == 1) rc = launch_stage(1, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
     if (rc) return HEOM_E_CUDA;
     ++r->launches;
     return timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y);
@@ -646,9 +654,16 @@ extern "C" int heom_observables(heom_run *r, double *out, int64_t cap_records, i
   if (!r || !out || cap_records < 0) { set_error("heom_observables: bad arguments"); return HEOM_E_ARG; }
   cudaError_t e = cudaStreamSynchronize(r->stream);
   if (e != cudaSuccess) return cuda_fail("heom_observables: stream", e);
-  int64_t cnt = 0;
-  e = cudaMemcpy(&cnt, r->rec_count, sizeof(int64_t), cudaMemcpyDeviceToHost);
+  int64_t cnt_err[2] = {0, 0};
+  e = cudaMemcpy(cnt_err, r->rec_count, sizeof(cnt_err), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail("heom_observables: counter", e);
+  int err_flag = 0;
+  std::memcpy(&err_flag, &cnt_err[1], sizeof(int));
+  if (err_flag) {
+    set_error("heom_observables: a device-side wait of the tensor-core stage kernel gave up (its results are invalid)");
+    return HEOM_E_TIMEOUT;
+  }
+  int64_t cnt = cnt_err[0];
   cnt = std::min(cnt, cap_records);
   const int rl = r->n + 5;
   if (cnt > 0) {

@@ -62,7 +62,15 @@ struct StageCommon {
   int n;
   int cplx_h;           // H has an imaginary part
   int herm;             // every ADO is Hermitian: gather row s only, and s H = (H s)^dagger
+  int *err;             // device flag: a bounded device-side wait gave up (tensor-core kernel)
 };
+
+// Tensor-core (split-TF32) form of the FP32 body stage: Hermitian runs with real H and N <= 16.
+// Returns 1 when it does not cover n_states.
+int launch_stage_tc_a(const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
+                      int sm_count);
+int launch_stage_tc_b(const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
+                      int sm_count);
 
 template <typename CT>
 struct StageArgs {

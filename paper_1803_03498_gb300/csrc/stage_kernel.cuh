@@ -308,6 +308,114 @@ __device__ __forceinline__ void apply_links(const LinkRec<CT> *rec, int64_t blo,
   }
 }
 
+// Owner-path link application for a Hermitian run: the first link batch (records in rec, gathers
+// landed), then further batches of at most cap records.  (rr, ri) hold row li of Q.
+template <int N, typename CT, typename BT>
+__device__ __forceinline__ void owner_apply(const StageCommon &c, const LinkRec<CT> *recs, int64_t rbase,
+                                            LinkRec<CT> *rec, typename Cplx<CT>::type *gbuf, unsigned char *tb,
+                                            int64_t lo, int64_t hi, int nrec, int cap, int u0, int lane,
+                                            CT (&rr)[N], CT (&ri)[N]) {
+  using R = LinkRec<CT>;
+  owner_links<N, CT>(rec, nrec, u0, lane, tb, gbuf, rr, ri);
+  for (int64_t blo = lo + nrec; blo < hi; blo += cap) {  // further link batches
+    __syncwarp();
+    const int nr = (int)min(hi - blo, (int64_t)cap);
+    warp_copy16(rec, recs + (blo - rbase), nr * (int)sizeof(R), lane);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    issue_gathers<N, CT, BT>(c, rec, nr, gbuf, lane);
+    cp_async_wait<0>();
+    __syncwarp();
+    owner_links<N, CT>(rec, nr, u0, lane, tb, gbuf, rr, ri);
+  }
+}
+
+// result_ij = Q_ij + conj(Q_ji) through the output tile zt_all (every lane must be done reading it);
+// (rr, ri) hold row li of Q on entry, the result row is left in zt_all.
+template <int N, typename CT, typename BT>
+__device__ __forceinline__ void owner_combine(bool active, int la, int li, typename Cplx<CT>::type *zt_all,
+                                              CT (&rr)[N], CT (&ri)[N]) {
+  using C2 = typename Cplx<CT>::type;
+  constexpr int EPO = StageShape<N, CT, BT>::EpOwn;
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      C2 w;
+      w.x = rr[j];
+      w.y = ri[j];
+      zt_all[la * EPO + li * N + j] = w;
+    }
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const C2 t = zt_all[la * EPO + j * N + li];
+      rr[j] += t.x;
+      ri[j] -= t.y;
+    }
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      C2 w;
+      w.x = rr[j];
+      w.y = ri[j];
+      zt_all[la * EPO + li * N + j] = w;
+    }
+  }
+}
+
+// out = y + ch * rhs (or ch * rhs) over the chunk's contiguous tiles [u0, u0 + cnt), 16 bytes per
+// access; rhs in the tile buffer ot, y in ybuf (or read from y_own when y is not staged).
+template <int N, typename CT, typename BT>
+__device__ __forceinline__ void store_chunk(typename Cplx<CT>::type *out_own, const typename Cplx<CT>::type *y_own,
+                                            int own0, int u0, int cnt, bool has_y, CT ch,
+                                            const typename Cplx<CT>::type *ot, const typename Cplx<CT>::type *ybuf,
+                                            int lane) {
+  using C2 = typename Cplx<CT>::type;
+  constexpr int EPO = StageShape<N, CT, BT>::EpOwn;
+  C2 *dst = out_own + (int64_t)(u0 - own0) * EPO;
+  if constexpr (sizeof(CT) == 4) {
+    const float4 *o4 = reinterpret_cast<const float4 *>(ot);
+    const float4 *y4 = kYSmem ? reinterpret_cast<const float4 *>(ybuf)
+                              : reinterpret_cast<const float4 *>(y_own + (int64_t)(u0 - own0) * EPO);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    const float chv = (float)ch;
+    for (int t = lane; t < cnt * EPO / 2; t += 32) {
+      float4 w = o4[t];
+      if (has_y) {
+        const float4 yv = y4[t];
+        w.x = fmaf(chv, w.x, yv.x);
+        w.y = fmaf(chv, w.y, yv.y);
+        w.z = fmaf(chv, w.z, yv.z);
+        w.w = fmaf(chv, w.w, yv.w);
+      } else {
+        w.x *= chv;
+        w.y *= chv;
+        w.z *= chv;
+        w.w *= chv;
+      }
+      d4[t] = w;
+    }
+  } else {
+    for (int t = lane; t < cnt * EPO; t += 32) {
+      C2 w = ot[t];
+      if (has_y) {
+        const C2 yv = kYSmem ? ybuf[t] : y_own[(int64_t)(u0 - own0) * EPO + t];
+        w.x = fma(ch, w.x, yv.x);
+        w.y = fma(ch, w.y, yv.y);
+      } else {
+        w.x *= ch;
+        w.y *= ch;
+      }
+      dst[t] = w;
+    }
+  }
+}
+
 template <int N, typename CT, typename BT, bool CPLX>
 __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kernel(const __grid_constant__ StageArgs<CT> a) {
   using S = StageShape<N, CT, BT>;
@@ -529,50 +637,8 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
     __syncwarp();
     if (own_path) {
       // Row li of Q in (rr, ri): -i H s, half the decay, and R v_{li, .} of the records of state li
-      unsigned char *tb = wb + W::tb;
-      owner_links<N, CT>(rec, nrec, u0, lane, tb, gbuf, rr, ri);
-      for (int64_t blo = lo + nrec; blo < hi; blo += cap) {  // further link batches
-        __syncwarp();
-        const int nr = (int)min(hi - blo, (int64_t)cap);
-        warp_copy16(rec, recs + (blo - rbase), nr * (int)sizeof(R), lane);
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncwarp();
-        issue_gathers<N, CT, BT>(c, rec, nr, gbuf, lane);
-        cp_async_wait<0>();
-        __syncwarp();
-        owner_links<N, CT>(rec, nr, u0, lane, tb, gbuf, rr, ri);
-      }
-      // result_ij = Q_ij + conj(Q_ji) through the tile (every lane is done reading it: the waits above
-      // end with __syncwarp)
-      if (active) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          C2 w;
-          w.x = rr[j];
-          w.y = ri[j];
-          zt_all[la * EPO + li * N + j] = w;
-        }
-      }
-      __syncwarp();
-      if (active) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const C2 t = zt_all[la * EPO + j * N + li];
-          rr[j] += t.x;
-          ri[j] -= t.y;
-        }
-      }
-      __syncwarp();
-      if (active) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          C2 w;
-          w.x = rr[j];
-          w.y = ri[j];
-          zt_all[la * EPO + li * N + j] = w;
-        }
-      }
+      owner_apply<N, CT, BT>(c, recs, rbase, rec, gbuf, wb + W::tb, lo, hi, nrec, cap, u0, lane, rr, ri);
+      owner_combine<N, CT, BT>(active, la, li, zt_all, rr, ri);
     } else {
       C2 *ot = zt_all + la * EPO;
       apply_links<N, CT, BT>(rec, lo, nrec, my_lo, my_hi, active, li, herm, ot, gbuf);
@@ -590,46 +656,7 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
       }
     }
     __syncwarp();
-    // y + ch * rhs over the chunk's contiguous tiles, 16 bytes per access
-    {
-      C2 *dst = out_own + (int64_t)(u0 - own0) * EPO;
-      if constexpr (sizeof(CT) == 4) {
-        const float4 *o4 = reinterpret_cast<const float4 *>(zt_all);
-        const float4 *y4 = kYSmem ? reinterpret_cast<const float4 *>(ybuf)
-                                  : reinterpret_cast<const float4 *>(y_own + (int64_t)(u0 - own0) * EPO);
-        float4 *d4 = reinterpret_cast<float4 *>(dst);
-        const float chv = (float)a.ch;
-        for (int t = lane; t < cnt * EPO / 2; t += 32) {
-          float4 w = o4[t];
-          if (has_y) {
-            const float4 yv = y4[t];
-            w.x = fmaf(chv, w.x, yv.x);
-            w.y = fmaf(chv, w.y, yv.y);
-            w.z = fmaf(chv, w.z, yv.z);
-            w.w = fmaf(chv, w.w, yv.w);
-          } else {
-            w.x *= chv;
-            w.y *= chv;
-            w.z *= chv;
-            w.w *= chv;
-          }
-          d4[t] = w;
-        }
-      } else {
-        for (int t = lane; t < cnt * EPO; t += 32) {
-          C2 w = zt_all[t];
-          if (has_y) {
-            const C2 yv = kYSmem ? ybuf[t] : y_own[(int64_t)(u0 - own0) * EPO + t];
-            w.x = fma(a.ch, w.x, yv.x);
-            w.y = fma(a.ch, w.y, yv.y);
-          } else {
-            w.x *= a.ch;
-            w.y *= a.ch;
-          }
-          dst[t] = w;
-        }
-      }
-    }
+    store_chunk<N, CT, BT>(out_own, y_own, own0, u0, cnt, has_y, a.ch, zt_all, ybuf, lane);
     __syncwarp();  // this tile buffer, record buffer and ybuf are reused by later chunks
     off_cur = off_nxt;
     off_nxt = off_nx2;

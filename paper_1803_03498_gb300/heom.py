@@ -16,8 +16,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libheom.so")
 
 HEOM_OK = 0
 HEOM_E_ARG, HEOM_E_OVERFLOW, HEOM_E_NOMEM, HEOM_E_CUDA, HEOM_E_TIMEOUT, HEOM_E_NUMERIC, HEOM_E_STATE = range(-1, -8, -1)
-FP64, FP32_MIXED = 0, 1
-PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
+FP64, FP32_MIXED, SPLIT_TF32 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED, "split_tf32": SPLIT_TF32}
 
 # every symbol include/heom.h declares
 ABI_SYMBOLS = [

@@ -70,6 +70,8 @@ def test_run_bytes_and_argument_errors(lib):
     h = heom.Hierarchy(p.system.n_modes, p.system.D)
     b64 = heom.run_bytes(p.system, h, "fp64", 10)
     b32 = heom.run_bytes(p.system, h, "fp32_mixed", 10)
+    # the split-TF32 precision stores exactly what the mixed precision stores
+    assert heom.run_bytes(p.system, h, "split_tf32", 10) == b32
     assert b64 > 0 and b32 > 0
     big = wl.lhcii_like().system
     hb = heom.Hierarchy(big.n_modes, big.D)
