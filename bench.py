@@ -342,7 +342,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 variant (0: steps/20)")
     ap.add_argument("--depth", type=int, default=0, help="override the hierarchy depth (profiling cases)")
-    ap.add_argument("--only", default="", choices=["", "mixed", "fp64"],
+    ap.add_argument("--tc-steps", type=int, default=0, help="timed steps of the split-TF32 variant (0: steps/10)")
+    ap.add_argument("--only", default="", choices=["", "mixed", "fp64", "split_tf32"],
                     help="time one precision only, no end-to-end or CPU legs (profiling cases)")
     args = ap.parse_args()
     ws, rank, local = _dist()
@@ -372,7 +373,7 @@ def main():
         prop.system.name = prop.system.name.replace("D=6", f"D={args.depth}")
     n_ado = prop.system.n_ado
     if args.only:
-        prec = "fp32_mixed" if args.only == "mixed" else "fp64"
+        prec = {"mixed": "fp32_mixed", "fp64": "fp64", "split_tf32": "split_tf32"}[args.only]
         ms, launches, kt, obs, _ = time_gpu(prop, prec, args.steps, args.warmup, ws, None)
         if rank == 0:
             print(json.dumps({"profile_case": prop.system.name, "precision": prec, "n_ado": n_ado,
@@ -397,6 +398,15 @@ def main():
     n = prop.system.N
     k = min(obs.shape[0], obs64.shape[0])
     pop_diff = float(np.max(np.abs(obs[:k, :n] - obs64[:k, :n])))  # same start, same first steps
+
+    # split-TF32 variant: the commutator of the FP32 body on the tensor cores (tcgen05)
+    tc_steps = args.tc_steps or max(3, args.steps // 10)
+    ms_tc, _, kt_tc, obs_tc, _ = time_gpu(prop, "split_tf32", tc_steps, 3, ws, None)
+    ms_tc = _max_over_ranks(ms_tc, ws)
+    v_tc = ws * n_ado * 4 * tc_steps / (ms_tc / 1000.0)
+    ach_tc = kt_tc["alg_bytes"] / (kt_tc["ms"] / 1000.0) / 1e9 if kt_tc["ms"] > 0 else 0.0
+    k = min(obs_tc.shape[0], obs64.shape[0])
+    pop_diff_tc = float(np.max(np.abs(obs_tc[:k, :n] - obs64[:k, :n])))
 
     # end to end through the public API (host buffers)
     hier = heom.Hierarchy(prop.system.n_modes, prop.system.D)
@@ -428,6 +438,12 @@ def main():
                                   "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": traffic64,
                                   "kernel": "stage_kernel<14,double,double>",
                                   "avg_launch_ms": kt64["ms"] / max(kt64["launches"], 1)}},
+            "split_tf32": {"value": v_tc, "unit": UNIT, "steps": tc_steps, "ms_per_step": ms_tc / tc_steps,
+                           "pop_diff_vs_fp64": pop_diff_tc,
+                           "roofline": {"bound": "hbm", "achieved": ach_tc, "peak": hbm_peak, "unit": "GB/s",
+                                        "frac": ach_tc / hbm_peak, "traffic": None,
+                                        "kernel": "stage_tc_kernel<14> (tcgen05.mma kind::tf32, levels >= 2)",
+                                        "avg_launch_ms": kt_tc["ms"] / max(kt_tc["launches"], 1)}},
             "mixed_vs_fp64_pop_diff": pop_diff,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "what": "heom_run_create from host arrays + propagate + observables to host, wall clock"},

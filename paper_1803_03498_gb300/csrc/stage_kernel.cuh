@@ -89,11 +89,12 @@ __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int byte
 #endif
 constexpr bool kYSmem = HEOM_Y_SMEM != 0;  // stage y tiles through shared memory
 
-template <int N, typename CT, typename BT>
+// RCO != 0 overrides the link records per batch (the tensor-core kernel sizes its own buffers).
+template <int N, typename CT, typename BT, int RCO = 0>
 struct StageShape {
   static constexpr int E = N * N;
   static constexpr int WARPS = sizeof(CT) == 8 ? HEOM_STAGE_WARPS_FP64 : HEOM_STAGE_WARPS;
-  static constexpr int RC = sizeof(CT) == 8 ? HEOM_REC_CAP_FP64 : (N <= 10 ? HEOM_REC_CAP_SMALL : HEOM_REC_CAP);
+  static constexpr int RC = RCO ? RCO : sizeof(CT) == 8 ? HEOM_REC_CAP_FP64 : (N <= 10 ? HEOM_REC_CAP_SMALL : HEOM_REC_CAP);
   static_assert(2 * RC <= 255, "owner table holds record indices in bytes");
   // ADOs per warp; at most 31 so that lanes 0..A hold the A + 1 record offsets of a chunk
   static constexpr int A = (32 / N < 32) ? 32 / N : 31;
@@ -107,9 +108,9 @@ struct StageShape {
 };
 
 // Per-warp shared-memory layout (byte offsets).
-template <int N, typename CT, typename BT>
+template <int N, typename CT, typename BT, int RCO = 0>
 struct WarpSmem {
-  using S = StageShape<N, CT, BT>;
+  using S = StageShape<N, CT, BT, RCO>;
   static constexpr int c2 = 2 * (int)sizeof(CT);
   static constexpr int tile_bytes = (S::A * S::EpOwn * c2 + 15) & ~15;
   static constexpr int rec_bytes = 2 * S::RC * (int)sizeof(LinkRec<CT>);  // Hermitian runs take 2 RC
@@ -209,7 +210,6 @@ template <int N, typename CT>
 __device__ __forceinline__ void owner_links(const LinkRec<CT> *rec, int nrec, int u0, int lane, unsigned char *tb,
                                             const typename Cplx<CT>::type *gbuf, CT (&rr)[N], CT (&ri)[N]) {
   using C2 = typename Cplx<CT>::type;
-  constexpr int kRounds = (2 * StageShape<N, CT, CT>::RC + 31) / 32;
   auto owner_of = [&](int t) -> int {
     if (t >= nrec) return -1;
     const int sw = rec[t].s;
@@ -220,7 +220,7 @@ __device__ __forceinline__ void owner_links(const LinkRec<CT> *rec, int nrec, in
   __syncwarp();
   int own = owner_of(lane);
   int before = -1;  // owner of record 32 r - 1
-  for (int r = 0; r < kRounds && 32 * r < nrec; ++r) {
+  for (int r = 0; 32 * r < nrec; ++r) {
     const int t = 32 * r + lane;
     const int nxt_round = owner_of(t + 32);
     int prev = __shfl_up_sync(0xffffffffu, own, 1);

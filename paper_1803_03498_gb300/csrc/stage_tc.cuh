@@ -7,17 +7,19 @@
 //
 // A CTA is 4 warps.  Each warp keeps the software pipeline of stage_kernel over its own chunks of
 // A = floor(32 / N) ADOs; the 4 warps meet once per chunk round, when lane (a, i) of warp w has written
-// row i of ADO a (real and imaginary parts, each split into TF32 high and low parts) as row 32 w + lane
-// of four 128 x 16 operand tiles in shared memory.  One thread then issues, per 8-wide K step,
+// row i of ADO a (real and imaginary parts, each split into TF32 high and low parts) into tensor-memory
+// lane 32 w + lane of four 16-column operand blocks (tcgen05.st; the A operand of the MMA sits in
+// tensor memory, so the shared memory holds only H).  One thread then issues, per 8-wide K step,
 //   D[:, 0:16)  += Re_hi H_hi + Re_lo H_hi + Re_hi H_lo
 //   D[:, 16:32) += Im_hi H_hi + Im_lo H_hi + Im_hi H_lo
 // as tcgen05.mma kind::tf32 (M = 128, N = 16, K = 8, FP32 accumulators in tensor memory) and commits
 // them to an mbarrier.  The tensor cores run while every warp gathers its linked neighbours and
 // applies the links; each warp then reads its 32 lanes of D (its own rows) with tcgen05.ld.  The
 // dropped lo * lo term and the TF32 rounding of the parts leave about 21 correct bits of S.
-// Operand tiles use the no-swizzle K-major layout: 8-row x 16-byte core matrices, the 4 core matrices
-// of one 8-row group adjacent (16 bytes apart in K: leading byte offset 128 B between K-adjacent core
-// matrices, stride byte offset 512 B between 8-row groups).
+// The B operand (H) uses the no-swizzle K-major shared-memory layout: 8-row x 16-byte core matrices,
+// the 4 core matrices of one 8-row group adjacent (leading byte offset 128 B between K-adjacent core
+// matrices, stride byte offset 512 B between 8-row groups).  Tensor memory of a CTA: columns 0-31 D
+// (real | imaginary part of S), 32-95 the A blocks Re_hi, Re_lo, Im_hi, Im_lo.
 // Every wait on the mbarrier gives up after about a second of clock cycles: the thread sets *c.err,
 // the CTA stops at the next round and frees its tensor memory; the host reports HEOM_E_TIMEOUT.
 #pragma once
@@ -31,15 +33,18 @@ namespace heom {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot_smem), "r"(ncols)
+// the column count is an immediate so that the kernel's tensor-memory use is known at compile time
+template <int NCOLS>
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_smem) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot_smem), "n"(NCOLS)
                : "memory");
 }
 __device__ __forceinline__ void tmem_relinquish() {
   asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
 }
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+template <int NCOLS>
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "n"(NCOLS) : "memory");
 }
 // D (tensor memory) = A B^T (+ D when acc != 0); A, B described by shared-memory descriptors
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -86,6 +91,25 @@ __device__ __forceinline__ float to_tf32(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
+// D (tensor memory) = A B^T (+ D when acc != 0); A in tensor memory (row m in lane m, K in columns),
+// B described by a shared-memory descriptor
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// 32 lanes x 16 columns of 32-bit tensor memory from one lane per thread of the warp
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};\n" ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 // 32 lanes x 32 columns of 32-bit tensor memory, one lane per thread of the warp, then wait
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&u)[32]) {
   asm volatile(
@@ -113,32 +137,38 @@ constexpr uint32_t tf32_idesc(int M, int Nn) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Nn >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+#ifndef HEOM_TC_REC_CAP
+#define HEOM_TC_REC_CAP 12  // link records per warp and batch (x2: Hermitian row-only slices)
+#endif
+#ifndef HEOM_TC_MIN_BLOCKS
+#define HEOM_TC_MIN_BLOCKS 4  // CTAs per SM the register allocation must allow (128 registers)
+#endif
+constexpr int kTcRC = HEOM_TC_REC_CAP;
 constexpr int kTcWarps = 4;                          // 128 rows of D, one TMEM lane quarter per warp
-constexpr int kTcCols = 32;                          // tensor-memory columns of a CTA: D re | im
+constexpr int kTcCols = 128;                         // tensor-memory columns of a CTA (96 used)
+constexpr int kTcA = 32;                             // first column of the A blocks
 constexpr int kTcK = 16;                             // N padded: the K and N extents of every MMA
 constexpr long long kTcWaitCycles = 2000000000LL;    // about a second at the GB300 SM clock
 
-// Byte offset of element (row m, column k) in a 16-wide K-major no-swizzle operand tile.
+// Byte offset of element (row m, column k) in a 16-wide K-major no-swizzle shared-memory operand.
 __device__ __forceinline__ int tc_off(int m, int k) {
   return ((m >> 3) * 4 + (k >> 2)) * 128 + (m & 7) * 16 + (k & 3) * 4;
 }
 
 // CTA-shared part of the dynamic shared memory (the per-warp stage buffers follow).
 struct TcSmem {
-  static constexpr int a_tile = 128 * kTcK * 4;  // 128 rows x 16 TF32
   static constexpr int b_tile = 16 * kTcK * 4;   // 16 rows x 16 TF32
-  static constexpr int a0 = 0;                   // Re_hi, Re_lo, Im_hi, Im_lo
-  static constexpr int b0 = 4 * a_tile;          // H_hi, H_lo
+  static constexpr int b0 = 0;                   // H_hi, H_lo
   static constexpr int mbar = b0 + 2 * b_tile;
   static constexpr int tslot = mbar + 8;         // tensor-memory address written by tcgen05.alloc
   static constexpr int total = (tslot + 4 + 127) & ~127;
 };
 
 template <int N>
-__global__ void __launch_bounds__(kTcWarps * 32) stage_tc_kernel(const __grid_constant__ StageArgs<float> a) {
+__global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_kernel(const __grid_constant__ StageArgs<float> a) {
   static_assert(N >= 1 && N <= kTcK, "the tensor-core form covers n_states <= 16");
-  using S = StageShape<N, float, float>;
-  using W = WarpSmem<N, float, float>;
+  using S = StageShape<N, float, float, kTcRC>;
+  using W = WarpSmem<N, float, float, kTcRC>;
   using C2 = float2;
   using R = LinkRec<float>;
   constexpr int A = S::A, EPO = S::EpOwn;
@@ -149,7 +179,7 @@ __global__ void __launch_bounds__(kTcWarps * 32) stage_tc_kernel(const __grid_co
   unsigned char *wb = smem_raw + TcSmem::total + warp * W::total;
   C2 *ybuf = reinterpret_cast<C2 *>(wb + W::ybuf);
   C2 *gbuf = reinterpret_cast<C2 *>(wb + W::gbuf);
-  const uint32_t a_base = smem_u32(cta + TcSmem::a0), b_base = smem_u32(cta + TcSmem::b0);
+  const uint32_t b_base = smem_u32(cta + TcSmem::b0);
   const uint32_t mbar = smem_u32(cta + TcSmem::mbar);
 
   // B operand: H split into TF32 parts, B[n][k] = H[k][n]; zero padding beyond N
@@ -165,7 +195,7 @@ __global__ void __launch_bounds__(kTcWarps * 32) stage_tc_kernel(const __grid_co
     mbar_init_fence();
   }
   if (warp == 0) {
-    tmem_alloc(smem_u32(cta + TcSmem::tslot), kTcCols);
+    tmem_alloc<kTcCols>(smem_u32(cta + TcSmem::tslot));
     tmem_relinquish();
   }
   fence_async_smem();
@@ -246,7 +276,7 @@ __global__ void __launch_bounds__(kTcWarps * 32) stage_tc_kernel(const __grid_co
       nrec = (int)min(hi - lo, (int64_t)cap);
     }
 
-    // own row s_{li, .} -> row 32 warp + lane of the four operand tiles (zeros for idle lanes)
+    // own row s_{li, .} -> tensor-memory lane 32 warp + lane of the four A blocks (zeros for idle lanes)
     C2 zr[N];
     {
       const C2 *zt = zt_all + la * EPO;
@@ -254,31 +284,24 @@ __global__ void __launch_bounds__(kTcWarps * 32) stage_tc_kernel(const __grid_co
 #pragma unroll
         for (int j = 0; j < N; ++j) zr[j] = zt[li * N + j];
       }
-      const int m = warp * 32 + lane;
+      uint32_t rh[kTcK], rl[kTcK], ih[kTcK], il[kTcK];
 #pragma unroll
-      for (int kc = 0; kc < kTcK / 4; ++kc) {
-        float4 rh, rl, ih, il;
-        float *prh = &rh.x, *prl = &rl.x, *pih = &ih.x, *pil = &il.x;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int k = kc * 4 + e;
-          const float xr = (k < N && active) ? zr[k < N ? k : 0].x : 0.f;
-          const float xi = (k < N && active) ? zr[k < N ? k : 0].y : 0.f;
-          const float hr = to_tf32(xr), hi2 = to_tf32(xi);
-          prh[e] = hr;
-          prl[e] = to_tf32(xr - hr);
-          pih[e] = hi2;
-          pil[e] = to_tf32(xi - hi2);
-        }
-        const int off = tc_off(m, kc * 4);
-        *reinterpret_cast<float4 *>(cta + TcSmem::a0 + 0 * TcSmem::a_tile + off) = rh;
-        *reinterpret_cast<float4 *>(cta + TcSmem::a0 + 1 * TcSmem::a_tile + off) = rl;
-        *reinterpret_cast<float4 *>(cta + TcSmem::a0 + 2 * TcSmem::a_tile + off) = ih;
-        *reinterpret_cast<float4 *>(cta + TcSmem::a0 + 3 * TcSmem::a_tile + off) = il;
+      for (int k = 0; k < kTcK; ++k) {
+        const float xr = (k < N && active) ? zr[k < N ? k : 0].x : 0.f;
+        const float xi = (k < N && active) ? zr[k < N ? k : 0].y : 0.f;
+        const float hr = to_tf32(xr), hi2 = to_tf32(xi);
+        rh[k] = __float_as_uint(hr);
+        rl[k] = __float_as_uint(to_tf32(xr - hr));
+        ih[k] = __float_as_uint(hi2);
+        il[k] = __float_as_uint(to_tf32(xi - hi2));
       }
+      tmem_st16(my_ld + kTcA + 0 * kTcK, rh);
+      tmem_st16(my_ld + kTcA + 1 * kTcK, rl);
+      tmem_st16(my_ld + kTcA + 2 * kTcK, ih);
+      tmem_st16(my_ld + kTcA + 3 * kTcK, il);
+      tmem_st_wait();
     }
-    fence_async_smem();
-    tc_fence_before();  // the previous round's tensor-memory reads precede the barrier
+    tc_fence_before();  // this warp's tensor-memory writes and reads precede the barrier
     failed = __syncthreads_or(failed);
     if (failed) break;
     if (threadIdx.x == 0) {
@@ -290,11 +313,11 @@ __global__ void __launch_bounds__(kTcWarps * 32) stage_tc_kernel(const __grid_co
 #pragma unroll
         for (int part = 0; part < 2; ++part) {  // real, imaginary part of s
           const uint32_t d = tmem + part * kTcK;
-          const uint64_t ah = smem_desc(a_base + (2 * part) * TcSmem::a_tile + ks * 256, 128, 512);
-          const uint64_t al = smem_desc(a_base + (2 * part + 1) * TcSmem::a_tile + ks * 256, 128, 512);
-          mma_tf32(d, ah, bh, idesc, ks > 0 ? 1u : 0u);
-          mma_tf32(d, al, bh, idesc, 1u);
-          mma_tf32(d, ah, bl, idesc, 1u);
+          const uint32_t ah = tmem + kTcA + (2 * part) * kTcK + ks * 8;
+          const uint32_t al = tmem + kTcA + (2 * part + 1) * kTcK + ks * 8;
+          mma_tf32_ta(d, ah, bh, idesc, ks > 0 ? 1u : 0u);
+          mma_tf32_ta(d, al, bh, idesc, 1u);
+          mma_tf32_ta(d, ah, bl, idesc, 1u);
         }
       }
       mma_commit(mbar);
@@ -357,7 +380,7 @@ __global__ void __launch_bounds__(kTcWarps * 32) stage_tc_kernel(const __grid_co
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, kTcCols);
+    tmem_dealloc<kTcCols>(tmem);
   }
 }
 
@@ -373,22 +396,34 @@ int launch_tc(const StageCommon &c, double ch, const double *term, const double 
   }
   for (int i = 0; i < c.n; ++i)
     for (int j = 0; j < c.n; ++j) a.H[i * kMaxStates + j] = (float)H[i * c.n + j];
-  const size_t smem = (size_t)TcSmem::total + (size_t)kTcWarps * WarpSmem<N, float, float>::total;
+  const size_t smem = (size_t)TcSmem::total + (size_t)kTcWarps * WarpSmem<N, float, float, kTcRC>::total;
+  // CTAs per SM from the kernel's registers, shared memory and tensor memory (the occupancy API
+  // answers 1 for kernels that allocate tensor memory; the persistent loop needs no co-residency, so
+  // a count above what fits only queues CTAs)
   static int per_sm = 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(stage_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, stage_tc_kernel<N>);
+    int dev = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     if (e != cudaSuccess) {
-      set_error(std::string("tensor-core stage kernel: shared memory attribute: ") + cudaGetErrorString(e));
+      set_error(std::string("tensor-core stage kernel: attributes: ") + cudaGetErrorString(e));
       return -4;
     }
-    int ps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, stage_tc_kernel<N>, kTcWarps * 32, smem);
-    if (e != cudaSuccess || ps < 1) {
-      set_error(std::string("tensor-core stage kernel: occupancy query failed or zero blocks: ") +
-                cudaGetErrorString(e));
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
+    const int by_regs = regs_sm / (regs_warp * kTcWarps);
+    const int by_smem = smem_sm / ((int)smem + smem_rsv);
+    const int by_tmem = 512 / kTcCols;
+    per_sm = std::min(std::min(by_regs, by_smem), by_tmem);
+    if (per_sm < 1) {
+      set_error("tensor-core stage kernel: does not fit on an SM");
+      per_sm = 0;
       return -4;
     }
-    per_sm = ps;
   }
   constexpr int A = StageShape<N, float, float>::A;
   const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
