@@ -523,42 +523,44 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
           ri[j] = 0;
           zr[j] = zt[li * N + j];
         }
-        // -i (H s)
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          const CT h = S::kRowRegs ? Hrow[S::kRowRegs ? k : 0] : a.H[li * kMaxStates + k];
-          if constexpr (S::kPairs) {
-            const float4 *zp = reinterpret_cast<const float4 *>(zt + k * N);
-#pragma unroll
-            for (int jp = 0; jp < N / 2; ++jp) {
-              const float4 z = zp[jp];
-              rr[2 * jp] = fma(h, z.y, rr[2 * jp]);
-              ri[2 * jp] = fma(-h, z.x, ri[2 * jp]);
-              rr[2 * jp + 1] = fma(h, z.w, rr[2 * jp + 1]);
-              ri[2 * jp + 1] = fma(-h, z.z, ri[2 * jp + 1]);
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-              const C2 z = zt[k * N + j];
-              rr[j] = fma(h, z.y, rr[j]);
-              ri[j] = fma(-h, z.x, ri[j]);
-            }
-          }
-        }
-        if constexpr (CPLX) {  // imaginary part of H in -i (H s)
+        if (!own_path) {
+          // -i (H s)
 #pragma unroll
           for (int k = 0; k < N; ++k) {
-            const CT h = a.Hi[li * kMaxStates + k];
+            const CT h = S::kRowRegs ? Hrow[S::kRowRegs ? k : 0] : a.H[li * kMaxStates + k];
+            if constexpr (S::kPairs) {
+              const float4 *zp = reinterpret_cast<const float4 *>(zt + k * N);
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-              const C2 z = zt[k * N + j];
-              rr[j] = fma(h, z.x, rr[j]);
-              ri[j] = fma(h, z.y, ri[j]);
+              for (int jp = 0; jp < N / 2; ++jp) {
+                const float4 z = zp[jp];
+                rr[2 * jp] = fma(h, z.y, rr[2 * jp]);
+                ri[2 * jp] = fma(-h, z.x, ri[2 * jp]);
+                rr[2 * jp + 1] = fma(h, z.w, rr[2 * jp + 1]);
+                ri[2 * jp + 1] = fma(-h, z.z, ri[2 * jp + 1]);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < N; ++j) {
+                const C2 z = zt[k * N + j];
+                rr[j] = fma(h, z.y, rr[j]);
+                ri[j] = fma(-h, z.x, ri[j]);
+              }
+            }
+          }
+          if constexpr (CPLX) {  // imaginary part of H in -i (H s)
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              const CT h = a.Hi[li * kMaxStates + k];
+#pragma unroll
+              for (int j = 0; j < N; ++j) {
+                const C2 z = zt[k * N + j];
+                rr[j] = fma(h, z.x, rr[j]);
+                ri[j] = fma(h, z.y, ri[j]);
+              }
             }
           }
         }
-        if (!herm) {  // + i (s H)
+        if (!herm || own_path) {  // + i (s H); on the owner path Q = i S with S = s H from the own row
 #pragma unroll
           for (int k = 0; k < N; ++k) {
             const C2 zk = zr[k];

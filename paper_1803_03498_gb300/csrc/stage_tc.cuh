@@ -15,7 +15,7 @@
 // as tcgen05.mma kind::tf32 (M = 128, N = 16, K = 8, FP32 accumulators in tensor memory) and commits
 // them to an mbarrier.  The tensor cores run while every warp gathers its linked neighbours and
 // applies the links; each warp then reads its 32 lanes of D (its own rows) with tcgen05.ld.  The
-// dropped lo * lo term and the TF32 rounding of the parts leave about 21 correct bits of S.
+// dropped lo * lo term and the TF32 width of the parts leave about 21 correct bits of S.
 // The B operand (H) uses the no-swizzle K-major shared-memory layout: 8-row x 16-byte core matrices,
 // the 4 core matrices of one 8-row group adjacent (leading byte offset 128 B between K-adjacent core
 // matrices, stride byte offset 512 B between 8-row groups).  Tensor memory of a CTA: columns 0-31 D
@@ -284,16 +284,18 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
 #pragma unroll
         for (int j = 0; j < N; ++j) zr[j] = zt[li * N + j];
       }
+      // x = hi + lo: hi = x rounded to the 10 explicit mantissa bits of TF32 (add half a TF32 unit to
+      // the magnitude bits, clear the 13 low bits), lo = x - hi exactly (|lo| <= 2^-11 |x|); the
+      // tensor core reads lo's top 19 bits, so the split keeps about 21 bits of x
       uint32_t rh[kTcK], rl[kTcK], ih[kTcK], il[kTcK];
 #pragma unroll
       for (int k = 0; k < kTcK; ++k) {
         const float xr = (k < N && active) ? zr[k < N ? k : 0].x : 0.f;
         const float xi = (k < N && active) ? zr[k < N ? k : 0].y : 0.f;
-        const float hr = to_tf32(xr), hi2 = to_tf32(xi);
-        rh[k] = __float_as_uint(hr);
-        rl[k] = __float_as_uint(to_tf32(xr - hr));
-        ih[k] = __float_as_uint(hi2);
-        il[k] = __float_as_uint(to_tf32(xi - hi2));
+        rh[k] = (__float_as_uint(xr) + 0x1000u) & 0xFFFFE000u;
+        ih[k] = (__float_as_uint(xi) + 0x1000u) & 0xFFFFE000u;
+        rl[k] = __float_as_uint(xr - __uint_as_float(rh[k]));
+        il[k] = __float_as_uint(xi - __uint_as_float(ih[k]));
       }
       tmem_st16(my_ld + kTcA + 0 * kTcK, rh);
       tmem_st16(my_ld + kTcA + 1 * kTcK, rl);
