@@ -388,6 +388,10 @@ def main():
     hbm_peak, peak_src = _peaks()
     traffic32, traffic64 = _traffic()
     ach = kt["alg_bytes"] / (kt["ms"] / 1000.0) / 1e9 if kt["ms"] > 0 else 0.0
+    # the classic-RK4 per-unit figure (4 tile transfers of N^2 FP32 complex plus 2 M 4-byte link-table
+    # entries per ADO-RHS evaluation) x the body ADOs of one launch, for comparison with `frac`
+    nb = n_ado - (1 + prop.system.n_modes)
+    unit4 = nb * (4.0 * prop.system.N ** 2 * 8 + 2 * prop.system.n_modes * 4)
 
     # FP64 variant
     f64_steps = args.fp64_steps or max(3, args.steps // 20)
@@ -429,6 +433,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                          "frac": ach / hbm_peak, "traffic": traffic32,
                          "alg_bytes_per_launch": kt["alg_bytes"] / max(kt["launches"], 1),
+                         "frac_per_unit_4_tiles": unit4 / (kt["ms"] / max(kt["launches"], 1) / 1000.0) / 1e9 / hbm_peak,
                          "kernel": "stage_kernel<14,float,float> (levels >= 2)",
                          "peak_source": peak_src, "timed_launches": kt["launches"],
                          "avg_launch_ms": kt["ms"] / max(kt["launches"], 1)},

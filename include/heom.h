@@ -70,10 +70,26 @@ typedef struct {
   const double *lambda_cm; /* [n_baths] reorganisation energy */
   const double *tau_fs;    /* [n_baths] correlation time 1/nu */
   const double *T_K;       /* [n_baths] temperature */
-  int n_matsubara;         /* K >= 0 */
+  int n_matsubara;         /* K >= 0: modes per bath beyond the Drude mode (Matsubara terms or Pade poles) */
   int terminator;
   int rescale;
+  int decomposition;       /* HEOM_MATSUBARA or HEOM_PADE */
 } heom_system;
+
+/* Expansion of the Bose function behind the bath modes (section "HEOM formalism"):
+ *   HEOM_MATSUBARA  gamma(b,k) = 2 pi k / beta, c(b,0) = lambda nu cot(beta nu / 2);
+ *   HEOM_PADE       the [K-1/K] Pade spectrum decomposition the paper uses (the method of its
+ *                   reference Hu, Xu, Yan 2010): xi_i = 2 / (i-th largest eigenvalue of the 2K x 2K
+ *                   tridiagonal Lambda, entries 1/sqrt((2m+1)(2m+3))), zeta_i likewise from the
+ *                   (2K-1) x (2K-1) Lambda' (entries 1/sqrt((2m+3)(2m+5))),
+ *                   eta_i = K (2K+3)/2 prod_j (zeta_j^2 - xi_i^2) / prod_{j != i} (xi_j^2 - xi_i^2),
+ *                   gamma(b,k) = xi_k / beta, c(b,k) = 4 lambda nu eta_k gamma_k / (beta (gamma_k^2 - nu^2)),
+ *                   c(b,0) = (2 lambda / beta) (1 - sum_j 2 eta_j nu^2 / (gamma_j^2 - nu^2)).
+ *                   The paper's printed c(b,0) sums over j but indexes eta_k, xi_k, and its eta
+ *                   numerator pairs zeta_j with xi_j; both are read as above (the form for which
+ *                   the approximant reproduces the Bose function). */
+#define HEOM_MATSUBARA 0
+#define HEOM_PADE 1
 
 /* Message of the calling thread's last failing call ("" if none).  Valid until that thread's next
  * call into the library. */
@@ -101,6 +117,18 @@ int heom_hier_info(const heom_hier *h, int64_t *n_ado, int64_t *level_offsets);
  * tuples[u][l] = n_l, plus[u][l] = index of n + e_l or -1 (|n| = depth),
  * minus[u][l] = index of n - e_l or -1 (n_l = 0).  Any pointer may be NULL. */
 int heom_hier_export(const heom_hier *h, uint8_t *tuples, int32_t *plus, int32_t *minus);
+
+/*
+ * heom_bath_modes -- the bath modes a run of this system uses (host only; no GPU needed).
+ *   Section "HEOM formalism": per bath b and k = 0..K, mode l = b (K+1) + k with rate gamma_l
+ *   (rad/fs), real coefficient c_l ((rad/fs)^2), lamnu_l = lambda_b nu_b for k = 0 else 0, and
+ *   the state s_b it couples to; term[s] = sum over the baths of state s of the terminator
+ *   2 lambda / (beta nu) - sum_k c(b,k) / gamma(b,k) (0 for every state when sys->terminator is 0).
+ *   Outputs (caller-owned host arrays): gamma, c, lamnu, mode_state [n_baths (K+1)], term [n_states].
+ *   Errors: HEOM_E_ARG for an invalid system or a rate gamma_k equal to nu (c_k diverges).
+ */
+int heom_bath_modes(const heom_system *sys, double *gamma, double *c, double *lamnu, int *mode_state,
+                    double *term);
 
 /*
  * heom_run_bytes -- device workspace bytes a run of this system, hierarchy and precision needs,

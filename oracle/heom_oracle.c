@@ -15,7 +15,8 @@
  *     level |n| and, inside a level, by colexicographic order of the stars-and-bars bar positions
  *     (a sort with an explicit comparator, not a ranking formula).
  *   - bath coefficients gamma(b,k), c(b,k) and the terminator: Eq. (HEOM) and its definitions
- *     (Matsubara expansion of a Drude-Lorentz density, Omega = 0).
+ *     (Matsubara expansion of a Drude-Lorentz density, Omega = 0), or the Pade expansion that
+ *     replaces them (same section, the Pade spectrum decomposition; see orc_pade).
  *   - right-hand side: Eq. (HEOM) term by term, with the superoperators V^x, V^x V^x and V^o
  *     written with the Kronecker deltas of their element-wise definitions, and the ADO rescaling
  *     (section "HEOM formalism", last two substitutions).
@@ -247,11 +248,89 @@ void orc_destroy(orc_model *m) {
   free(m);
 }
 
-/* H_re/H_im: [N][N] row-major in cm^-1 (H_im may be NULL).  Returns NULL on bad input. */
+/* Eigenvalues of the symmetric n x n matrix a (row-major, overwritten) by cyclic Jacobi rotations:
+ * each rotation in the (p, q) plane zeroes a_pq; sweeps repeat until the off-diagonal part vanishes.
+ * ev receives the diagonal, i.e. the eigenvalues, in no particular order. */
+static void jacobi_eigenvalues(double *a, int n, double *ev) {
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += a[p * n + q] * a[p * n + q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = a[p * n + q];
+        if (apq == 0.0) continue;
+        double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) { /* columns p, q */
+          double akp = a[k * n + p], akq = a[k * n + q];
+          a[k * n + p] = c * akp - s * akq;
+          a[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) { /* rows p, q */
+          double apk = a[p * n + k], aqk = a[q * n + k];
+          a[p * n + k] = c * apk - s * aqk;
+          a[q * n + k] = s * apk + c * aqk;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) ev[i] = a[i * n + i];
+}
+
+static int desc_cmp(const void *x, const void *y) {
+  double a = *(const double *)x, b = *(const double *)y;
+  return (a < b) - (a > b);
+}
+
+/* Pade spectrum decomposition of the Bose function used by the paper (section "HEOM formalism", the
+ * Pade expansion it takes from its reference Hu, Xu, Yan 2010):
+ *   1/(1 - exp(-x)) ~ 1/x + 1/2 + sum_{i=1..K} 2 eta_i x / (x^2 + xi_i^2)
+ * with xi_i = 2 / (i-th largest eigenvalue of Lambda), Lambda_{m,m+1} = 1/sqrt((2m+1)(2m+3)),
+ * m = 1..2K; zeta_j likewise from Lambda' (size 2K-1, entries 1/sqrt((2m+3)(2m+5)));
+ * eta_i = K (2K+3)/2 prod_{j<K} (zeta_j^2 - xi_i^2) / prod_{j != i} (xi_j^2 - xi_i^2).
+ * (The paper's printed eta pairs zeta_j with xi_j; it is read with xi_i, the form for which the
+ * sum above reproduces the Bose function.)  xi, eta: [K].  Returns 0, or -1 for K < 1. */
+int orc_pade(int K, double *xi, double *eta) {
+  if (K < 1) return -1;
+  int n = 2 * K, n2 = 2 * K - 1;
+  double *a = (double *)calloc((size_t)n * n, sizeof(double));
+  double *ev = (double *)malloc(sizeof(double) * n);
+  double *zeta = (double *)malloc(sizeof(double) * (K > 1 ? K - 1 : 1));
+  for (int m = 1; m < n; ++m) a[(m - 1) * n + m] = a[m * n + m - 1] = 1.0 / sqrt((2.0 * m + 1) * (2.0 * m + 3));
+  jacobi_eigenvalues(a, n, ev);
+  qsort(ev, n, sizeof(double), desc_cmp);
+  for (int i = 0; i < K; ++i) xi[i] = 2.0 / ev[i];
+  if (K > 1) {
+    memset(a, 0, sizeof(double) * (size_t)n * n);
+    for (int m = 1; m < n2; ++m) a[(m - 1) * n2 + m] = a[m * n2 + m - 1] = 1.0 / sqrt((2.0 * m + 3) * (2.0 * m + 5));
+    jacobi_eigenvalues(a, n2, ev);
+    qsort(ev, n2, sizeof(double), desc_cmp);
+    for (int j = 0; j < K - 1; ++j) zeta[j] = 2.0 / ev[j];
+  }
+  for (int i = 0; i < K; ++i) {
+    double num = 1.0, den = 1.0;
+    for (int j = 0; j < K - 1; ++j) num *= zeta[j] * zeta[j] - xi[i] * xi[i];
+    for (int j = 0; j < K; ++j)
+      if (j != i) den *= xi[j] * xi[j] - xi[i] * xi[i];
+    eta[i] = K * (2.0 * K + 3.0) / 2.0 * num / den;
+  }
+  free(a);
+  free(ev);
+  free(zeta);
+  return 0;
+}
+
+/* H_re/H_im: [N][N] row-major in cm^-1 (H_im may be NULL).  decomposition 0: Matsubara expansion,
+ * 1: Pade expansion with K poles.  Returns NULL on bad input. */
 orc_model *orc_create(int N, const double *H_re, const double *H_im, int B, const int *bath_state,
                       const double *lambda_cm, const double *tau_fs, const double *T_K, int K,
-                      int D, int terminator, int rescale) {
-  if (N < 1 || B < 1 || K < 0 || D < 0) return NULL;
+                      int D, int terminator, int rescale, int decomposition) {
+  if (N < 1 || B < 1 || K < 0 || D < 0 || decomposition < 0 || decomposition > 1) return NULL;
+  double pxi[64], peta[64];
+  if (decomposition == 1 && K > 64) return NULL;
+  if (decomposition == 1 && K > 0) orc_pade(K, pxi, peta);
   orc_model *m = (orc_model *)calloc(1, sizeof(orc_model));
   m->N = N;
   m->B = B;
@@ -283,11 +362,25 @@ orc_model *orc_create(int N, const double *H_re, const double *H_im, int B, cons
       double g, c;
       if (k == 0) {
         g = nu;                                      /* gamma(b,0) = nu_b */
-        c = nu * lam / tan(beta * nu / 2.0);         /* c(b,0) = nu lambda cot(beta nu / 2) */
+        if (decomposition == 0) {
+          c = nu * lam / tan(beta * nu / 2.0);       /* c(b,0) = nu lambda cot(beta nu / 2) */
+        } else {                                     /* c(b,0) = 2 lambda / beta (1 - sum_j ...) */
+          double sum = 0.0;
+          for (int j = 0; j < K; ++j) {
+            double gj = pxi[j] / beta;
+            sum += 2.0 * peta[j] * nu * nu / (gj * gj - nu * nu);
+          }
+          c = 2.0 * lam / beta * (1.0 - sum);
+        }
       } else {
-        g = 2.0 * ORC_PI * k / beta;                   /* gamma(b,k) = 2 pi k / beta */
+        if (decomposition == 0) {
+          g = 2.0 * ORC_PI * k / beta;                 /* gamma(b,k) = 2 pi k / beta */
+        } else {
+          g = pxi[k - 1] / beta;                       /* gamma(b,k) = xi_k / beta */
+        }
         if (fabs(g * g - nu * nu) < 1e-6 * g * g) { orc_destroy(m); return NULL; } /* gamma_k = nu */
         c = 4.0 * lam * nu / beta * g / (g * g - nu * nu);
+        if (decomposition == 1) c *= peta[k - 1];    /* c(b,k) = ... eta_k ... */
       }
       m->gamma[l] = g;
       m->c[l] = c;

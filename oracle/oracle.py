@@ -56,7 +56,9 @@ def lib():
         L.orc_hier_export.argtypes = [ctypes.c_int, ctypes.c_int, i64, P(u8), P(i32), P(i32)]
         L.orc_hier_export.restype = ctypes.c_int
         L.orc_create.argtypes = [ctypes.c_int, P(d), P(d), ctypes.c_int, P(ctypes.c_int), P(d), P(d), P(d),
-                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_pade.argtypes = [ctypes.c_int, P(d), P(d)]
+        L.orc_pade.restype = ctypes.c_int
         L.orc_create.restype = vp
         L.orc_destroy.argtypes = [vp]
         L.orc_destroy.restype = None
@@ -109,14 +111,25 @@ class Bath:
     T_K: float          # temperature, K
 
 
+def pade(K):
+    """Pade poles xi and weights eta of the Bose function (orc_pade): 1/(1 - e^-x) ~ 1/x + 1/2 +
+    sum_i 2 eta_i x / (x^2 + xi_i^2)."""
+    xi = np.zeros(K)
+    eta = np.zeros(K)
+    if lib().orc_pade(int(K), _ptr(xi, ctypes.c_double), _ptr(eta, ctypes.c_double)):
+        raise ValueError("K must be >= 1")
+    return xi, eta
+
+
 @dataclass
 class OracleModel:
     H: np.ndarray                 # [N, N] complex or real, cm^-1
     baths: list                   # list[Bath]
-    K: int                        # Matsubara terms beyond the Drude term
+    K: int                        # modes per bath beyond the Drude mode (Matsubara terms or Pade poles)
     D: int                        # hierarchy depth
     terminator: bool = True
     rescale: bool = True
+    decomposition: str = "matsubara"  # or "pade"
     _h: int = field(default=0, init=False, repr=False)
 
     def __post_init__(self):
@@ -131,7 +144,8 @@ class OracleModel:
         Ta = np.array([b.T_K for b in self.baths], dtype=np.float64)
         h = lib().orc_create(self.N, _ptr(hr, ctypes.c_double), _ptr(hi, ctypes.c_double), B,
                              _ptr(st, ctypes.c_int), _ptr(la, ctypes.c_double), _ptr(ta, ctypes.c_double),
-                             _ptr(Ta, ctypes.c_double), self.K, self.D, int(self.terminator), int(self.rescale))
+                             _ptr(Ta, ctypes.c_double), self.K, self.D, int(self.terminator), int(self.rescale),
+                             {"matsubara": 0, "pade": 1}[self.decomposition])
         if not h:
             raise ValueError("oracle rejected the model (bad shape, state index or Matsubara resonance)")
         self._h = h

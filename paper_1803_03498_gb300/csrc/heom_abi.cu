@@ -140,8 +140,9 @@ struct Layout {
 
 inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int check_system(const heom_system *s, const heom_hier *h, int precision) {
-  if (!s || !h) { set_error("NULL system or hierarchy"); return HEOM_E_ARG; }
+// The system alone (no hierarchy, no precision).
+int check_system_only(const heom_system *s) {
+  if (!s) { set_error("NULL system"); return HEOM_E_ARG; }
   if (s->n_states < 1 || s->n_states > kMaxStates) {
     set_error("n_states must be in [1, 24]");
     return HEOM_E_ARG;
@@ -149,10 +150,6 @@ int check_system(const heom_system *s, const heom_hier *h, int precision) {
   if (!s->H_re) { set_error("H_re is NULL"); return HEOM_E_ARG; }
   if (s->n_baths < 1 || !s->bath_state || !s->lambda_cm || !s->tau_fs || !s->T_K || s->n_matsubara < 0) {
     set_error("need n_baths >= 1, bath arrays and n_matsubara >= 0");
-    return HEOM_E_ARG;
-  }
-  if ((int64_t)s->n_baths * (s->n_matsubara + 1) != h->h.M) {
-    set_error("hierarchy n_modes != n_baths * (n_matsubara + 1)");
     return HEOM_E_ARG;
   }
   for (int b = 0; b < s->n_baths; ++b) {
@@ -165,9 +162,137 @@ int check_system(const heom_system *s, const heom_hier *h, int precision) {
       return HEOM_E_ARG;
     }
   }
+  if (s->decomposition != HEOM_MATSUBARA && s->decomposition != HEOM_PADE) {
+    set_error("decomposition must be HEOM_MATSUBARA or HEOM_PADE");
+    return HEOM_E_ARG;
+  }
+  if (s->decomposition == HEOM_PADE && s->n_matsubara > 64) {
+    set_error("at most 64 Pade poles per bath");
+    return HEOM_E_ARG;
+  }
+  return HEOM_OK;
+}
+
+int check_system(const heom_system *s, const heom_hier *h, int precision) {
+  if (!s || !h) { set_error("NULL system or hierarchy"); return HEOM_E_ARG; }
+  int rc = check_system_only(s);
+  if (rc) return rc;
+  if ((int64_t)s->n_baths * (s->n_matsubara + 1) != h->h.M) {
+    set_error("hierarchy n_modes != n_baths * (n_matsubara + 1)");
+    return HEOM_E_ARG;
+  }
   if (precision != HEOM_FP64 && precision != HEOM_FP32_MIXED && precision != HEOM_SPLIT_TF32) {
     set_error("unknown precision");
     return HEOM_E_ARG;
+  }
+  return HEOM_OK;
+}
+
+// Eigenvalues of the symmetric tridiagonal matrix with zero diagonal and off-diagonal e[0..n-2],
+// in decreasing order, by bisection on the Sturm count (number of eigenvalues below x from the
+// signs of the LDL^T pivots of T - x I).
+static std::vector<double> tridiag_eigs_desc(const std::vector<double> &e, int n) {
+  double bound = 0;
+  for (double v : e) bound = std::max(bound, 2.0 * std::fabs(v));
+  bound += 1e-12;
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double q = -x;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < n; ++i) {
+      if (q == 0) q = 1e-300;
+      q = -x - e[i - 1] * e[i - 1] / q;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  std::vector<double> ev(n);
+  for (int k = 0; k < n; ++k) {  // k-th largest: n - 1 - k eigenvalues lie below it
+    double lo = -bound, hi = bound;
+    for (int it = 0; it < 200 && hi - lo > 1e-17 * std::max(1.0, std::fabs(hi)); ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (count_below(mid) > n - 1 - k) hi = mid;
+      else lo = mid;
+    }
+    ev[k] = 0.5 * (lo + hi);
+  }
+  return ev;
+}
+
+// [K-1/K] Pade poles xi and weights eta of the Bose function (section "HEOM formalism", method of
+// Hu, Xu, Yan 2010): 1/(1 - e^-x) ~ 1/x + 1/2 + sum_i 2 eta_i x / (x^2 + xi_i^2).
+static void pade_poles(int K, std::vector<double> &xi, std::vector<double> &eta) {
+  xi.assign(K, 0.0);
+  eta.assign(K, 0.0);
+  if (K < 1) return;
+  std::vector<double> e1(2 * K - 1), e2(std::max(0, 2 * K - 2));
+  for (int m = 1; m < 2 * K; ++m) e1[m - 1] = 1.0 / std::sqrt((2.0 * m + 1) * (2.0 * m + 3));
+  for (int m = 1; m < 2 * K - 1; ++m) e2[m - 1] = 1.0 / std::sqrt((2.0 * m + 3) * (2.0 * m + 5));
+  const std::vector<double> l1 = tridiag_eigs_desc(e1, 2 * K);
+  const std::vector<double> l2 = K > 1 ? tridiag_eigs_desc(e2, 2 * K - 1) : std::vector<double>();
+  std::vector<double> zeta(std::max(0, K - 1));
+  for (int i = 0; i < K; ++i) xi[i] = 2.0 / l1[i];
+  for (int i = 0; i < K - 1; ++i) zeta[i] = 2.0 / l2[i];
+  for (int i = 0; i < K; ++i) {
+    double num = 1.0, den = 1.0;
+    for (int j = 0; j < K - 1; ++j) num *= zeta[j] * zeta[j] - xi[i] * xi[i];
+    for (int j = 0; j < K; ++j)
+      if (j != i) den *= xi[j] * xi[j] - xi[i] * xi[i];
+    eta[i] = 0.5 * K * (2.0 * K + 3.0) * num / den;
+  }
+}
+
+// Bath modes of Eq. HEOM (Drude-Lorentz, Omega = 0) in rad/fs: rates, real coefficients, lambda nu
+// of the Drude modes, coupled states, per-state terminator; gmax = the largest rate.
+static int compute_modes(const heom_system *sys, std::vector<double> &gam, std::vector<double> &cc,
+                         std::vector<double> &lnu, std::vector<int> &mstate, std::vector<double> &term,
+                         double *gmax) {
+  const int B = sys->n_baths, K = sys->n_matsubara, M = B * (K + 1);
+  gam.assign(M, 0.0);
+  cc.assign(M, 0.0);
+  lnu.assign(M, 0.0);
+  mstate.assign(M, 0);
+  term.assign(sys->n_states, 0.0);
+  *gmax = 0;
+  std::vector<double> xi, eta;
+  if (sys->decomposition == HEOM_PADE) pade_poles(K, xi, eta);
+  for (int b = 0; b < B; ++b) {
+    const double lam = kCmToRadFs * sys->lambda_cm[b];
+    const double nu = 1.0 / sys->tau_fs[b];
+    const double beta = 1.0 / (kCmToRadFs * kBoltzCm * sys->T_K[b]);
+    double csum = 0;
+    for (int k = 0; k <= K; ++k) {
+      const int l = b * (K + 1) + k;
+      double g = nu, c = 0;
+      if (k > 0) {
+        g = (sys->decomposition == HEOM_PADE) ? xi[k - 1] / beta : 2.0 * 3.14159265358979323846 * k / beta;
+        if (std::fabs(g * g - nu * nu) < 1e-6 * g * g) {
+          set_error("bath rate gamma_k equals nu for a bath (c_k diverges)");
+          return HEOM_E_ARG;
+        }
+        c = 4.0 * lam * nu / beta * g / (g * g - nu * nu) * (sys->decomposition == HEOM_PADE ? eta[k - 1] : 1.0);
+      }
+      gam[l] = g;
+      cc[l] = c;
+      lnu[l] = (k == 0) ? lam * nu : 0.0;
+      mstate[l] = sys->bath_state[b];
+    }
+    if (sys->decomposition == HEOM_PADE) {  // c(b,0) = (2 lambda / beta) (1 - sum_j 2 eta_j nu^2 / (gamma_j^2 - nu^2))
+      double s = 0;
+      for (int j = 0; j < K; ++j) {
+        const double gj = gam[b * (K + 1) + 1 + j];
+        s += 2.0 * eta[j] * nu * nu / (gj * gj - nu * nu);
+      }
+      cc[b * (K + 1)] = 2.0 * lam / beta * (1.0 - s);
+    } else {
+      cc[b * (K + 1)] = lam * nu / std::tan(0.5 * beta * nu);
+    }
+    for (int k = 0; k <= K; ++k) {
+      const int l = b * (K + 1) + k;
+      csum += cc[l] / gam[l];
+      *gmax = std::max(*gmax, gam[l]);
+    }
+    if (sys->terminator) term[sys->bath_state[b]] += 2.0 * lam / (beta * nu) - csum;
   }
   return HEOM_OK;
 }
@@ -217,6 +342,28 @@ int cuda_fail(const char *what, cudaError_t e) {
 }
 
 }  // namespace
+
+extern "C" int heom_bath_modes(const heom_system *sys, double *gamma, double *c, double *lamnu, int *mode_state,
+                               double *term) {
+  int rc = check_system_only(sys);
+  if (rc) return rc;
+  if (!gamma || !c || !lamnu || !mode_state || !term) {
+    set_error("heom_bath_modes: NULL output array");
+    return HEOM_E_ARG;
+  }
+  std::vector<double> gam, cc, lnu, tm;
+  std::vector<int> ms;
+  double gmax = 0;
+  if ((rc = compute_modes(sys, gam, cc, lnu, ms, tm, &gmax))) return rc;
+  for (size_t l = 0; l < gam.size(); ++l) {
+    gamma[l] = gam[l];
+    c[l] = cc[l];
+    lamnu[l] = lnu[l];
+    mode_state[l] = ms[l];
+  }
+  for (size_t i = 0; i < tm.size(); ++i) term[i] = tm[i];
+  return HEOM_OK;
+}
 
 extern "C" int heom_run_bytes(const heom_system *sys, const heom_hier *h, int precision, int64_t max_records,
                               size_t *bytes) {
@@ -317,39 +464,13 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
           (sys->H_im && sys->H_im[i * n + j] != -sys->H_im[j * n + i]))
         r->herm = false;
 
-  // ---- Matsubara coefficients of Eq. HEOM (Drude-Lorentz, Omega = 0), terminator and rescaling
-  std::vector<double> gam(M), cc(M), lnu(M);
-  std::vector<int> mstate(M);
-  r->term.assign(n, 0.0);
+  // ---- bath modes of Eq. HEOM (Drude-Lorentz, Omega = 0), terminator and rescaling
+  std::vector<double> gam, cc, lnu;
+  std::vector<int> mstate;
   double gmax = 0;
-  for (int b = 0; b < B; ++b) {
-    const double lam = kCmToRadFs * sys->lambda_cm[b];
-    const double nu = 1.0 / sys->tau_fs[b];
-    const double beta = 1.0 / (kCmToRadFs * kBoltzCm * sys->T_K[b]);
-    double csum = 0;
-    for (int k = 0; k <= K; ++k) {
-      const int l = b * (K + 1) + k;
-      double g, c;
-      if (k == 0) {
-        g = nu;
-        c = lam * nu / std::tan(0.5 * beta * nu);
-      } else {
-        g = 2.0 * 3.14159265358979323846 * k / beta;
-        if (std::fabs(g * g - nu * nu) < 1e-6 * g * g) {
-          delete r;
-          set_error("Matsubara frequency gamma_k equals nu for a bath (c_k diverges)");
-          return HEOM_E_ARG;
-        }
-        c = 4.0 * lam * nu / beta * g / (g * g - nu * nu);
-      }
-      gam[l] = g;
-      cc[l] = c;
-      lnu[l] = (k == 0) ? lam * nu : 0.0;
-      mstate[l] = sys->bath_state[b];
-      csum += c / g;
-      gmax = std::max(gmax, g);
-    }
-    if (sys->terminator) r->term[sys->bath_state[b]] += 2.0 * lam / (beta * nu) - csum;
+  if (compute_modes(sys, gam, cc, lnu, mstate, r->term, &gmax)) {
+    delete r;
+    return HEOM_E_ARG;
   }
   r->max_rate = D * gmax;
 

@@ -25,8 +25,10 @@ ABI_SYMBOLS = [
     "heom_run_bytes", "heom_run_create", "heom_run_destroy", "heom_propagate", "heom_record_len",
     "heom_observables", "heom_get_sigma0", "heom_get_ados", "heom_set_ados", "heom_rhs_eval", "heom_run_info",
     "heom_run_launches", "heom_run_set_timing", "heom_run_kernel_time", "heom_propagate_static",
-    "heom_batch_create", "heom_batch_launch", "heom_batch_destroy",
+    "heom_batch_create", "heom_batch_launch", "heom_batch_destroy", "heom_bath_modes",
 ]
+MATSUBARA, PADE = 0, 1
+DECOMPOSITIONS = {"matsubara": MATSUBARA, "pade": PADE}
 
 
 class HeomError(RuntimeError):
@@ -48,6 +50,7 @@ class _System(ctypes.Structure):
         ("n_matsubara", ctypes.c_int),
         ("terminator", ctypes.c_int),
         ("rescale", ctypes.c_int),
+        ("decomposition", ctypes.c_int),
     ]
 
 
@@ -159,7 +162,22 @@ class _SysArgs:
         s.n_matsubara = int(system.K)
         s.terminator = int(bool(terminator))
         s.rescale = int(bool(rescale))
+        s.decomposition = DECOMPOSITIONS[getattr(system, "decomposition", "matsubara")]
         self.s = s
+
+
+def bath_modes(system, terminator=True):
+    """Bath modes the library uses for `system` (host only): dict of gamma, c, lamnu [rad/fs units],
+    mode_state (per mode) and term (per state)."""
+    L = load()
+    sa = _SysArgs(system, terminator=terminator)
+    M = len(system.bath_state) * (system.K + 1)
+    g, c, ln = (np.zeros(M) for _ in range(3))
+    ms = np.zeros(M, dtype=np.intc)
+    term = np.zeros(system.N)
+    _check(L.heom_bath_modes(ctypes.byref(sa.s), _dp(g), _dp(c), _dp(ln),
+                             ms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(term)))
+    return {"gamma": g, "c": c, "lamnu": ln, "mode_state": ms, "term": term}
 
 
 def run_bytes(system, hier: Hierarchy, precision="fp64", max_records=1, terminator=True, rescale=True) -> int:

@@ -17,6 +17,8 @@ Energies are in cm^-1, times in fs, temperatures in K.  The workloads:
                     1/nu U[50, 200], T in {77, 300}; three dipole orientations each.
 * ``serving_stream`` -- Poisson arrivals of requests, N in {2..24}, D in {2..6}, K in {0, 1},
                     200..5000 steps.
+* ``cd_runs``    -- three circular-dichroism runs of a site system, pigment centres from
+                    ``site_positions`` (uniform in a 30 Angstrom cube; FMO-like: seed 1803022).
 The FMO Hamiltonian printed in the paper (section "Results", FMO seven-pigment model) is
 available as a fixed extra input from ``tests/golden``; it is not used by the benchmarks.
 """
@@ -37,8 +39,9 @@ class System:
     lambda_cm: list
     tau_fs: list
     T_K: list
-    K: int                        # Matsubara terms beyond the Drude term (modes per bath = K + 1)
+    K: int                        # modes per bath beyond the Drude mode (modes per bath = K + 1)
     D: int                        # hierarchy depth
+    decomposition: str = "matsubara"  # expansion of the Bose function: "matsubara" or "pade"
 
     @property
     def N(self) -> int:
@@ -115,6 +118,30 @@ def dipole_runs(sysm_sites: System, dip: np.ndarray, dt_fs: float, n_steps: int,
         re = np.zeros((n + 1, n + 1))
         re[:, 0] = w            # sigma_0(0) = mu_p^+ |0><0|
         out.append(Propagation(g, re, np.zeros_like(re), dt_fs, n_steps, w=w, tag=f"{tag}-dip{p}"))
+    return out
+
+
+def site_positions(rng, n_sites, box_angstrom: float = 30.0):
+    """Pigment centres R_a, uniform in a cube of the given edge (Angstrom), centred at the origin."""
+    return rng.uniform(-0.5 * box_angstrom, 0.5 * box_angstrom, (n_sites, 3))
+
+
+def cd_runs(sysm_sites: System, dip: np.ndarray, pos: np.ndarray, dt_fs: float, n_steps: int, tag: str):
+    """Three circular-dichroism runs (Cartesian e_p) on the (N+1)-state space: sigma_0(0) has the
+    rotational strengths (R_a x d_a) . e_p in column 0, the recorded correlation weights are
+    e_p . d_a (mu_p^-)."""
+    Hg, _ = with_ground_state(sysm_sites.H)
+    n = sysm_sites.N
+    g = System(sysm_sites.name + " +ground", Hg, [s + 1 for s in sysm_sites.bath_state], list(sysm_sites.lambda_cm),
+               list(sysm_sites.tau_fs), list(sysm_sites.T_K), sysm_sites.K, sysm_sites.D)
+    rot = np.cross(pos, dip)
+    out = []
+    for p in range(3):
+        w = np.zeros(n + 1)
+        w[1:] = dip[:, p]
+        re = np.zeros((n + 1, n + 1))
+        re[1:, 0] = rot[:, p]
+        out.append(Propagation(g, re, np.zeros_like(re), dt_fs, n_steps, w=w, tag=f"{tag}-cd{p}"))
     return out
 
 
