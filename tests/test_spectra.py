@@ -78,3 +78,17 @@ def test_circular_dichroism_is_conservative():
     dw = (e_cm[1] - e_cm[0]) * spectra.TWO_PI_C
     assert abs(np.sum(cd) * dw / (2 * np.pi)) <= 1e-12 * np.sum(np.abs(cd)) * dw
     assert np.max(np.abs(cd)) > 1.0  # not trivially zero
+
+
+def test_boltzmann_state():
+    """exp(-H0/kT)/Z with H0 = H minus the reorganisation energies: trace 1, commutes with H0, and for a
+    diagonal H0 the populations are the Boltzmann factors."""
+    pop, _ = wl.fmo_like()
+    s = pop.system
+    rho = spectra.boltzmann_state(s)
+    H0 = s.H - np.diag(s.lambda_cm)
+    assert abs(np.trace(rho) - 1.0) <= 1e-14
+    assert np.max(np.abs(rho @ H0 - H0 @ rho)) <= 1e-10
+    d = wl.System("diag", np.diag([0.0, 100.0, 250.0]), [0, 1, 2], [35.0] * 3, [50.0] * 3, [300.0] * 3, K=0, D=1)
+    p = np.exp(-np.array([0.0, 100.0, 250.0]) / (0.6950348004 * 300.0))
+    assert np.allclose(np.diag(spectra.boltzmann_state(d)), p / p.sum(), rtol=1e-13, atol=0)
