@@ -122,13 +122,21 @@ def _dist():
 
 
 def _max_over_ranks(x, ws):
+    """The largest x over the ranks (each rank times its own replica; the job takes the slowest)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _job_value(ws, n_ado, steps, ms_max):
+    """Whole-job ADO-RHS evaluations per second: every rank runs one replica of n_ado ADOs for `steps`
+    RK4 steps (4 RHS evaluations each); the job's time is the slowest rank's."""
+    return ws * n_ado * 4 * steps / (ms_max / 1000.0)
 
 
 def _barrier(ws):
@@ -384,7 +392,7 @@ def main():
     # headline: mixed precision
     ms, launches, kt, obs, clk = time_gpu(prop, "fp32_mixed", args.steps, args.warmup, ws, clocks)
     ms_max = _max_over_ranks(ms, ws)
-    value = ws * n_ado * 4 * args.steps / (ms_max / 1000.0)
+    value = _job_value(ws, n_ado, args.steps, ms_max)
     hbm_peak, peak_src = _peaks()
     traffic32, traffic64 = _traffic()
     ach = kt["alg_bytes"] / (kt["ms"] / 1000.0) / 1e9 if kt["ms"] > 0 else 0.0
@@ -397,7 +405,7 @@ def main():
     f64_steps = args.fp64_steps or max(3, args.steps // 20)
     ms64, l64, kt64, obs64, _ = time_gpu(prop, "fp64", f64_steps, 3, ws, None)
     ms64 = _max_over_ranks(ms64, ws)
-    v64 = ws * n_ado * 4 * f64_steps / (ms64 / 1000.0)
+    v64 = _job_value(ws, n_ado, f64_steps, ms64)
     ach64 = kt64["alg_flops"] / (kt64["ms"] / 1000.0) / 1e12 if kt64["ms"] > 0 else 0.0
     n = prop.system.N
     k = min(obs.shape[0], obs64.shape[0])
@@ -407,7 +415,7 @@ def main():
     tc_steps = args.tc_steps or max(3, args.steps // 10)
     ms_tc, _, kt_tc, obs_tc, _ = time_gpu(prop, "split_tf32", tc_steps, 3, ws, None)
     ms_tc = _max_over_ranks(ms_tc, ws)
-    v_tc = ws * n_ado * 4 * tc_steps / (ms_tc / 1000.0)
+    v_tc = _job_value(ws, n_ado, tc_steps, ms_tc)
     ach_tc = kt_tc["alg_bytes"] / (kt_tc["ms"] / 1000.0) / 1e9 if kt_tc["ms"] > 0 else 0.0
     k = min(obs_tc.shape[0], obs64.shape[0])
     pop_diff_tc = float(np.max(np.abs(obs_tc[:k, :n] - obs64[:k, :n])))
@@ -416,7 +424,7 @@ def main():
     hier = heom.Hierarchy(prop.system.n_modes, prop.system.D)
     t_e2e, h2d, d2h = time_e2e(prop, "fp32_mixed", args.steps, hier)
     t_e2e = _max_over_ranks(t_e2e, ws)
-    e2e_value = ws * n_ado * 4 * args.steps / t_e2e
+    e2e_value = _job_value(ws, n_ado, args.steps, 1000.0 * t_e2e)
 
     line = None
     if rank == 0:
