@@ -199,6 +199,16 @@ int heom_rhs_eval(heom_run *r, int64_t u0, int64_t count, double *re, double *im
 int heom_run_info(const heom_run *r, int64_t *n_ado, int *n_states, int *n_modes, int64_t *steps_done,
                   double *t_fs);
 
+/*
+ * heom_run_layout -- how the run stores its ADOs: 0 = N x N matrices; 1 = the excited-ground
+ *   coherence block, each ADO stored as its column 0 (chosen at creation when state 0 has no bath,
+ *   H has no element between state 0 and the others, and rho(0) lives on column 0 below the
+ *   diagonal: a linear-absorption run; every term of Eq. HEOM keeps every ADO in that block, so the
+ *   right-hand side acts on columns, with the same results).  heom_set_ados with data outside the
+ *   block moves the run to layout 0 for good.  -1 for a NULL run.
+ */
+int heom_run_layout(const heom_run *r);
+
 /* Kernel launches the library enqueued for this run since creation (all kinds). */
 int64_t heom_run_launches(const heom_run *r);
 

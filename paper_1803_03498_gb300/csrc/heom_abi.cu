@@ -57,6 +57,9 @@ struct heom_run {
   std::vector<double> H, Hi;         // shifted Re H, Im H
   bool cplx_h = false;
   bool herm = false;                 // every ADO Hermitian (Hermitian H and data; paper gauge)
+  bool vec = false;                  // every ADO in the coherence block |a><0|: stored as its column 0
+  size_t copy_bytes = 0;             // bytes of one state copy (head + body, matrix layout)
+  double bytes_full_y = 0, bytes_full_noy = 0, flops_full = 0;  // matrix-layout accounting
   std::vector<double> term;          // per state
   double max_rate = 0;               // D * max gamma
   // device
@@ -377,11 +380,11 @@ extern "C" int heom_run_bytes(const heom_system *sys, const heom_hier *h, int pr
 }
 
 namespace heom {
-__global__ void record_kernel(StateView y, int u_split, int body_fp32, int n, const double *w, double *records,
+__global__ void record_kernel(StateView y, int u_split, int body_fp32, int vec, int n, const double *w, double *records,
                               int64_t *rec_count, int64_t max_records);
-__global__ void scatter_kernel(StateView dst, int Ep, int u_split, int body_fp32, int n, int64_t u0, int64_t count,
+__global__ void scatter_kernel(StateView dst, int Ep, int u_split, int body_fp32, int vec, int n, int64_t u0, int64_t count,
                                const double *re, const double *im);
-__global__ void gather_kernel(StateView src, int Ep, int u_split, int body_fp32, int n, int64_t u0, int64_t count,
+__global__ void gather_kernel(StateView src, int Ep, int u_split, int body_fp32, int vec, int n, int64_t u0, int64_t count,
                               double *re, double *im);
 }  // namespace heom
 
@@ -397,7 +400,7 @@ static int enqueue_record(heom_run *r) {
     set_error("observable record buffer full (max_records)");
     return HEOM_E_NOMEM;
   }
-  record_kernel<<<1, 32, 0, r->stream>>>(r->y, r->u_split, r->precision != HEOM_FP64, r->n, r->w_dev, r->records,
+  record_kernel<<<1, 32, 0, r->stream>>>(r->y, r->u_split, r->precision != HEOM_FP64, r->vec, r->n, r->w_dev, r->records,
                                          r->rec_count, r->max_records);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail("record kernel launch", e);
@@ -463,6 +466,17 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
       if (sys->H_re[i * n + j] != sys->H_re[j * n + i] ||
           (sys->H_im && sys->H_im[i * n + j] != -sys->H_im[j * n + i]))
         r->herm = false;
+
+  // ---- coherence block (linear-absorption runs): state 0 without a bath, no H element between state
+  // 0 and the others, rho(0) supported on column 0 below the diagonal; every ADO then stays of the
+  // form sum_a x_a |a><0| and is stored and propagated as that column (vec_kernel.cuh)
+  r->vec = n >= 2 && !r->cplx_h;
+  for (int b = 0; b < B && r->vec; ++b) r->vec = sys->bath_state[b] != 0;
+  for (int a = 1; a < n && r->vec; ++a) r->vec = sys->H_re[a] == 0.0 && sys->H_re[a * n] == 0.0;
+  for (int i = 0; i < n && r->vec; ++i)
+    for (int j = 0; j < n && r->vec; ++j)
+      if (!(j == 0 && i > 0)) r->vec = sigma0_re[i * n + j] == 0.0 && (!sigma0_im || sigma0_im[i * n + j] == 0.0);
+  if (r->vec) r->herm = false;
 
   // ---- bath modes of Eq. HEOM (Drude-Lorentz, Omega = 0), terminator and rescaling
   std::vector<double> gam, cc, lnu;
@@ -569,6 +583,14 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     const double links = up * 8.0 * (n - 1) + dn * 8.0 * (2 * n - 1);
     r->flops_gen = nb * (comm + 8.0 * E) + links;
     r->flops_herm = nb * (0.5 * comm + 8.0 * E) + links;
+    r->bytes_full_y = r->bytes_stage_y;
+    r->bytes_full_noy = r->bytes_stage_noy;
+    r->flops_full = r->flops_gen;
+    if (r->vec) {  // column 0 only: N elements per ADO, 8 N^2 flops of H x, one complex FMA per link
+      r->bytes_stage_y = nb * 3.0 * n * cs + tab;
+      r->bytes_stage_noy = nb * 2.0 * n * cs + tab;
+      r->flops_gen = r->flops_herm = nb * (8.0 * n * n + 8.0 * n) + (up + dn) * 8.0;
+    }
   }
 
   char *base = reinterpret_cast<char *>(device_workspace);
@@ -579,6 +601,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   r->records = reinterpret_cast<double *>(base + L.off_rec);
   r->w_dev = reinterpret_cast<double *>(base + L.off_w);
   r->rec_count = reinterpret_cast<int64_t *>(base + L.off_cnt);
+  r->copy_bytes = L.head_bytes + L.body_bytes;
   r->err_dev = reinterpret_cast<int *>(base + L.off_cnt + sizeof(int64_t));
   r->y = view_at(base, L, 0);
   r->zA = view_at(base, L, 1);
@@ -675,6 +698,24 @@ static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, dou
   int rc;
   const bool same_y = (y.head == zin.head && y.body == zin.body);
   const bool no_y = (y.head == nullptr && y.body == nullptr);
+  if (r->vec) {  // coherence block: column-0 kernels
+    if (r->precision != HEOM_FP64) {
+      c.u_begin = 0;
+      c.u_end = r->u_split;
+      rc = launch_stage_vec(2, c, ch, r->term.data(), r->H.data(), r->stream, r->sm_count);
+      if (rc) return HEOM_E_CUDA;
+      ++r->launches;
+    }
+    c.u_begin = (r->precision == HEOM_FP64) ? 0 : r->u_split;
+    c.u_end = (int)r->n_ado;
+    if (c.u_end <= c.u_begin) return HEOM_OK;
+    if ((rc = timed_begin(r))) return rc;
+    rc = launch_stage_vec(r->precision == HEOM_FP64 ? 0 : 1, c, ch, r->term.data(), r->H.data(), r->stream,
+                          r->sm_count);
+    if (rc) return HEOM_E_CUDA;
+    ++r->launches;
+    return timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y);
+  }
   if (r->precision == HEOM_FP64) {
     c.u_begin = 0;
     c.u_end = (int)r->n_ado;
@@ -827,7 +868,7 @@ static int io_range(heom_run *r, StateView state, int64_t u0, int64_t count, dou
       if (e == cudaSuccess) e = cudaMemcpyAsync(st_im, im + c0 * E, cc * E * sizeof(double), cudaMemcpyHostToDevice, r->stream);
       if (e != cudaSuccess) return cuda_fail("state upload", e);
       const int blocks = (int)std::min<int64_t>((cc * E + 255) / 256, 65535);
-      scatter_kernel<<<blocks, 256, 0, r->stream>>>(state, r->Ep, r->u_split, r->precision != HEOM_FP64, r->n, u0 + c0,
+      scatter_kernel<<<blocks, 256, 0, r->stream>>>(state, r->Ep, r->u_split, r->precision != HEOM_FP64, r->vec, r->n, u0 + c0,
                                                    cc, st_re, st_im);
       ++r->launches;
       e = cudaGetLastError();
@@ -836,7 +877,7 @@ static int io_range(heom_run *r, StateView state, int64_t u0, int64_t count, dou
       if (e != cudaSuccess) return cuda_fail("state upload sync", e);
     } else {
       const int blocks = (int)std::min<int64_t>((cc * E + 255) / 256, 65535);
-      gather_kernel<<<blocks, 256, 0, r->stream>>>(state, r->Ep, r->u_split, r->precision != HEOM_FP64, r->n, u0 + c0,
+      gather_kernel<<<blocks, 256, 0, r->stream>>>(state, r->Ep, r->u_split, r->precision != HEOM_FP64, r->vec, r->n, u0 + c0,
                                                   cc, st_re, st_im);
       ++r->launches;
       e = cudaGetLastError();
@@ -850,8 +891,50 @@ static int io_range(heom_run *r, StateView state, int64_t u0, int64_t count, dou
   return HEOM_OK;
 }
 
+// Leaves the coherence-block layout for good: the current state moves to the matrix layout (through
+// zA and host memory, in chunks), then the run uses the matrix kernels.
+static int leave_vec(heom_run *r) {
+  cudaError_t e = cudaMemcpyAsync(r->zA.head, r->y.head, r->copy_bytes, cudaMemcpyDeviceToDevice, r->stream);
+  if (e != cudaSuccess) return cuda_fail("layout change copy", e);
+  const int64_t E = (int64_t)r->n * r->n;
+  const int64_t chunk = std::max<int64_t>(1, (int64_t)((64u << 20) / (2 * sizeof(double) * E)));
+  std::vector<double> hr, hi;
+  try {
+    hr.resize((size_t)std::min(chunk, r->n_ado) * E);
+    hi.resize(hr.size());
+  } catch (...) {
+    set_error("host allocation failed (layout change)");
+    return HEOM_E_NOMEM;
+  }
+  for (int64_t u0 = 0; u0 < r->n_ado; u0 += chunk) {
+    const int64_t cc = std::min(chunk, r->n_ado - u0);
+    r->vec = true;
+    int rc = io_range(r, r->zA, u0, cc, hr.data(), hi.data(), false);
+    r->vec = false;
+    if (!rc) rc = io_range(r, r->y, u0, cc, hr.data(), hi.data(), true);
+    if (rc) return rc;
+  }
+  r->bytes_stage_y = r->bytes_full_y;
+  r->bytes_stage_noy = r->bytes_full_noy;
+  r->flops_gen = r->flops_full;
+  r->flops_herm = r->flops_full;
+  return HEOM_OK;
+}
+
 extern "C" int heom_set_ados(heom_run *r, int64_t u0, int64_t count, const double *re, const double *im) {
   if (!r) { set_error("heom_set_ados: NULL run"); return HEOM_E_ARG; }
+  if (r->vec && re && im) {  // data outside the coherence block ends the column-0 layout
+    const int n = r->n;
+    bool in_block = true;
+    for (int64_t k = 0; k < count * n * n && in_block; ++k) {
+      const int64_t e = k % ((int64_t)n * n), i = e / n, j = e % n;
+      if (!(j == 0 && i > 0) && (re[k] != 0.0 || im[k] != 0.0)) in_block = false;
+    }
+    if (!in_block) {
+      int rc = leave_vec(r);
+      if (rc) return rc;
+    }
+  }
   if (r->herm && re && im) {  // a non-Hermitian ADO switches the run to the general kernels for good
     const int n = r->n;
     for (int64_t c = 0; c < count && r->herm; ++c) {
@@ -897,6 +980,8 @@ extern "C" int heom_run_info(const heom_run *r, int64_t *n_ado, int *n_states, i
   return HEOM_OK;
 }
 
+extern "C" int heom_run_layout(const heom_run *r) { return r ? (r->vec ? 1 : 0) : -1; }
+
 extern "C" int64_t heom_run_launches(const heom_run *r) { return r ? r->launches : -1; }
 
 // ------------------------------------------------------------------------------------------------
@@ -914,8 +999,17 @@ __device__ __forceinline__ double2 ld_any(const StateView &s, int E, int Ep, int
   return reinterpret_cast<const double2 *>(s.body)[(v - u_split) * Ep + e];
 }
 
+// Element e = i n + j of ADO v in the run's layout: matrix tiles, or (vec) column 0 only.
+__device__ __forceinline__ double2 ld_elem(const StateView &s, int n, int Ep, int u_split, int body_fp32, int vec,
+                                           int64_t v, int64_t e) {
+  if (!vec) return ld_any(s, n * n, Ep, u_split, body_fp32, v, e);
+  const int64_t i = e / n, j = e - i * n;
+  if (j != 0) return make_double2(0.0, 0.0);
+  return ld_any(s, n, n, u_split, body_fp32, v, i);
+}
+
 // One observable record of sigma_0 (FP64): populations, trace, dipole correlation, Hermiticity.
-__global__ void record_kernel(StateView y, int u_split, int body_fp32, int n, const double *w, double *records,
+__global__ void record_kernel(StateView y, int u_split, int body_fp32, int vec, int n, const double *w, double *records,
                               int64_t *rec_count, int64_t max_records) {
   if (threadIdx.x != 0) return;
   const int64_t idx = *rec_count;
@@ -924,16 +1018,16 @@ __global__ void record_kernel(StateView y, int u_split, int body_fp32, int n, co
   double *rec = records + idx * (n + 5);
   double tr = 0, ti = 0, cr = 0, ci = 0, herm = 0;
   for (int a = 0; a < n; ++a) {
-    const double2 d = ld_any(y, E, E, u_split, body_fp32, 0, (int64_t)a * n + a);
+    const double2 d = ld_elem(y, n, E, u_split, body_fp32, vec, 0, (int64_t)a * n + a);
     rec[a] = d.x;
     tr += d.x;
     ti += d.y;
-    const double2 c0 = ld_any(y, E, E, u_split, body_fp32, 0, (int64_t)a * n);
+    const double2 c0 = ld_elem(y, n, E, u_split, body_fp32, vec, 0, (int64_t)a * n);
     cr += w[a] * c0.x;
     ci += w[a] * c0.y;
     for (int b = 0; b < n; ++b) {
-      const double2 x = ld_any(y, E, E, u_split, body_fp32, 0, (int64_t)a * n + b);
-      const double2 z = ld_any(y, E, E, u_split, body_fp32, 0, (int64_t)b * n + a);
+      const double2 x = ld_elem(y, n, E, u_split, body_fp32, vec, 0, (int64_t)a * n + b);
+      const double2 z = ld_elem(y, n, E, u_split, body_fp32, vec, 0, (int64_t)b * n + a);
       herm = fmax(herm, hypot(x.x - z.x, x.y + z.y));
     }
   }
@@ -945,28 +1039,36 @@ __global__ void record_kernel(StateView y, int u_split, int body_fp32, int n, co
   *rec_count = idx + 1;
 }
 
-__global__ void scatter_kernel(StateView dst, int Ep, int u_split, int body_fp32, int n, int64_t u0, int64_t count,
+__global__ void scatter_kernel(StateView dst, int Ep, int u_split, int body_fp32, int vec, int n, int64_t u0, int64_t count,
                                const double *re, const double *im) {
   const int64_t E = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count * E; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = t / E, e = t - c * E;
+    const int64_t c = t / E;
+    int64_t e = t - c * E;
     const int64_t v = u0 + c;
+    int64_t TE = E, TP = Ep;
+    if (vec) {  // column 0 only (the host checked that the rest is zero)
+      if (e % n != 0) continue;
+      e /= n;
+      TE = n;
+      TP = n;
+    }
     if (v < u_split) {
-      dst.head[v * E + e] = make_double2(re[t], im[t]);
+      dst.head[v * TE + e] = make_double2(re[t], im[t]);
     } else if (body_fp32) {
-      reinterpret_cast<float2 *>(dst.body)[(v - u_split) * Ep + e] = make_float2((float)re[t], (float)im[t]);
+      reinterpret_cast<float2 *>(dst.body)[(v - u_split) * TP + e] = make_float2((float)re[t], (float)im[t]);
     } else {
-      reinterpret_cast<double2 *>(dst.body)[(v - u_split) * Ep + e] = make_double2(re[t], im[t]);
+      reinterpret_cast<double2 *>(dst.body)[(v - u_split) * TP + e] = make_double2(re[t], im[t]);
     }
   }
 }
 
-__global__ void gather_kernel(StateView src, int Ep, int u_split, int body_fp32, int n, int64_t u0, int64_t count,
+__global__ void gather_kernel(StateView src, int Ep, int u_split, int body_fp32, int vec, int n, int64_t u0, int64_t count,
                               double *re, double *im) {
   const int64_t E = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count * E; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = t / E, e = t - c * E;
-    const double2 d = ld_any(src, (int)E, Ep, u_split, body_fp32, u0 + c, e);
+    const double2 d = ld_elem(src, n, Ep, u_split, body_fp32, vec, u0 + c, e);
     re[t] = d.x;
     im[t] = d.y;
   }

@@ -65,6 +65,11 @@ struct StageCommon {
   int *err;             // device flag: a bounded device-side wait gave up (tensor-core kernel)
 };
 
+// Coherence-block (column-0) stage kernels (vec_stage.cu): kind 0 FP64, 1 mixed body (FP32),
+// 2 mixed head (FP64 compute, FP32 body neighbours).
+int launch_stage_vec(int kind, const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
+                     int sm_count);
+
 // Tensor-core (split-TF32) form of the FP32 body stage: Hermitian runs with real H and N <= 16.
 // Returns 1 when it does not cover n_states.
 int launch_stage_tc_a(const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,

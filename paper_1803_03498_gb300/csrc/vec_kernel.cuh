@@ -1,0 +1,164 @@
+// Stage kernel for runs in the excited-ground coherence block (linear-absorption runs).
+//
+// When state 0 carries no bath, H has no element between state 0 and the others, and every ADO
+// starts in span{|a><0| : a != 0} (a dipole run: sigma_0(0) = mu^+ |0><0|, all other ADOs zero),
+// every term of Eq. HEOM (arXiv 1803.03498, section "HEOM formalism") keeps every ADO in that block:
+// the commutator maps |a><0| to sum_b H_ba |b><0| - |a><0| H_00, and V_s = |s><s| with s != 0 acts on
+// |a><0| only through its row (V_s |a><0| = delta_sa |s><0|, |a><0| V_s = 0).  Each ADO is then the
+// column x_a = sigma[a][0] (x_0 = 0), and its right-hand side is
+//     (L x)_a = -i sum_b (H_ab - H_00 delta_ab) x_b - (sum_l n_l gamma_l + Delta_a) x_a
+//               + sum over the links of u through a mode of state a of R v_a
+// with the link coefficients R of the full form (its column part and diagonal part vanish here).
+// out_u = y_u + ch (L zin)_u as in stage_kernel (Horner RK4).  Lane (a, i) of a warp holds element i
+// of ADO u0 + a (A = floor(32 / N) ADOs per warp); H x goes through warp shuffles, each lane applies
+// the links of its own state (the records of an ADO are ordered by state).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "heom_internal.h"
+
+namespace heom {
+
+template <typename T>
+struct VCplx;
+template <>
+struct VCplx<float> {
+  using type = float2;
+};
+template <>
+struct VCplx<double> {
+  using type = double2;
+};
+
+constexpr int kVecWarps = 8;  // warps per CTA
+
+// Element s of ADO v's column from the head (FP64) or body (storage type BT) region, as CT.
+template <int N, typename CT, typename BT>
+__device__ __forceinline__ typename VCplx<CT>::type vec_load(const StateView &s, int u_split, int64_t v, int e) {
+  typename VCplx<CT>::type r;
+  if (v < u_split) {
+    const double2 d = s.head[v * N + e];
+    r.x = (CT)d.x;
+    r.y = (CT)d.y;
+  } else {
+    const typename VCplx<BT>::type b = reinterpret_cast<const typename VCplx<BT>::type *>(s.body)[(v - u_split) * N + e];
+    r.x = (CT)b.x;
+    r.y = (CT)b.y;
+  }
+  return r;
+}
+
+// kOwnHead: CT = double, BT = float -- the FP64 head kernel of a mixed-precision run (its own ADOs
+// are in the head region); otherwise the own ADOs are in the body region of storage type BT == CT.
+template <int N, typename CT, typename BT>
+__global__ void __launch_bounds__(kVecWarps * 32) vec_stage_kernel(const __grid_constant__ StageArgs<CT> a) {
+  using C2 = typename VCplx<CT>::type;
+  constexpr int A = 32 / N;
+  constexpr bool kOwnHead = sizeof(CT) == 8 && sizeof(BT) == 4;
+  const StageCommon &c = a.c;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kVecWarps + (threadIdx.x >> 5);
+  const int nw = gridDim.x * kVecWarps;
+  const int la = lane / N, li = lane - la * N;
+  const bool lane_ok = la < A;
+  const bool has_y = (c.y.head != nullptr) || (c.y.body != nullptr);
+  const LinkRec<CT> *recs = reinterpret_cast<const LinkRec<CT> *>(kOwnHead ? c.recs_head : c.recs_body);
+  const int64_t rbase = kOwnHead ? 0 : c.rec_split;
+  CT hrow[N];
+#pragma unroll
+  for (int b = 0; b < N; ++b) hrow[b] = lane_ok ? a.H[li * kMaxStates + b] : (CT)0;
+  const CT h00 = a.H[0];
+  const CT term_i = lane_ok ? a.term[li] : (CT)0;
+  const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
+  for (int chn = gw; chn < n_chunks; chn += nw) {
+    const int u0 = c.u_begin + chn * A;
+    const int cnt = min(A, c.u_end - u0);
+    const bool active = lane_ok && la < cnt;
+    const int64_t u = u0 + la;
+    C2 x;
+    x.x = 0;
+    x.y = 0;
+    C2 yv = x;
+    if (active) {
+      x = vec_load<N, CT, BT>(c.zin, c.u_split, u, li);
+      if (has_y) yv = vec_load<N, CT, BT>(c.y, c.u_split, u, li);
+    }
+    // -i (H x)_i + i H_00 x_i
+    CT rr = -h00 * x.y, ri = h00 * x.x;
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      const CT xr = __shfl_sync(0xffffffffu, x.x, min(la, A - 1) * N + b);
+      const CT xi = __shfl_sync(0xffffffffu, x.y, min(la, A - 1) * N + b);
+      rr = fma(hrow[b], xi, rr);
+      ri = fma(-hrow[b], xr, ri);
+    }
+    if (active) {
+      const CT f = (CT)c.gsum[u] + term_i;
+      rr = fma(-f, x.x, rr);
+      ri = fma(-f, x.y, ri);
+      if (li > 0) {  // links of state li: records of ADO u are ordered by state
+        const int64_t lo = c.link_off[u], hi = c.link_off[u + 1];
+        for (int64_t p = lo; p < hi; ++p) {
+          const LinkRec<CT> r = recs[p - rbase];
+          const int s = r.s & kRecStateMask;
+          if (s < li) continue;
+          if (s > li) break;
+          const C2 v = vec_load<N, CT, BT>(c.zin, c.u_split, r.v, li);
+          rr = fma(r.re, v.x, fma(-r.im, v.y, rr));
+          ri = fma(r.re, v.y, fma(r.im, v.x, ri));
+        }
+      }
+      C2 o;
+      o.x = has_y ? fma(a.ch, rr, yv.x) : a.ch * rr;
+      o.y = has_y ? fma(a.ch, ri, yv.y) : a.ch * ri;
+      if (kOwnHead || u < c.u_split) {
+        c.out.head[u * N + li] = make_double2((double)o.x, (double)o.y);
+      } else {
+        typename VCplx<BT>::type w;
+        w.x = (BT)o.x;
+        w.y = (BT)o.y;
+        reinterpret_cast<typename VCplx<BT>::type *>(c.out.body)[(u - c.u_split) * N + li] = w;
+      }
+    }
+  }
+}
+
+template <int N, typename CT, typename BT>
+int launch_vec_n(const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
+                 int sm_count) {
+  StageArgs<CT> a;
+  a.c = c;
+  a.ch = (CT)ch;
+  for (int i = 0; i < kMaxStates; ++i) a.term[i] = (i < c.n) ? (CT)term[i] : (CT)0;
+  for (int i = 0; i < kMaxStates * kMaxStates; ++i) {
+    a.H[i] = 0;
+    a.Hi[i] = 0;
+  }
+  for (int i = 0; i < c.n; ++i)
+    for (int j = 0; j < c.n; ++j) a.H[i * kMaxStates + j] = (CT)H[i * c.n + j];
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int ps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, vec_stage_kernel<N, CT, BT>, kVecWarps * 32, 0);
+    if (e != cudaSuccess || ps < 1) {
+      set_error(std::string("vector stage kernel: occupancy query failed: ") + cudaGetErrorString(e));
+      return -4;
+    }
+    per_sm = ps;
+  }
+  constexpr int A = 32 / N;
+  const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
+  const int grid = std::max(1, std::min((n_chunks + kVecWarps - 1) / kVecWarps, per_sm * sm_count));
+  vec_stage_kernel<N, CT, BT><<<grid, kVecWarps * 32, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("vector stage kernel launch: ") + cudaGetErrorString(e));
+    return -4;
+  }
+  return 0;
+}
+
+}  // namespace heom

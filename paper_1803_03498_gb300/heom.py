@@ -25,7 +25,7 @@ ABI_SYMBOLS = [
     "heom_run_bytes", "heom_run_create", "heom_run_destroy", "heom_propagate", "heom_record_len",
     "heom_observables", "heom_get_sigma0", "heom_get_ados", "heom_set_ados", "heom_rhs_eval", "heom_run_info",
     "heom_run_launches", "heom_run_set_timing", "heom_run_kernel_time", "heom_propagate_static",
-    "heom_batch_create", "heom_batch_launch", "heom_batch_destroy", "heom_bath_modes",
+    "heom_batch_create", "heom_batch_launch", "heom_batch_destroy", "heom_bath_modes", "heom_run_layout",
 ]
 MATSUBARA, PADE = 0, 1
 DECOMPOSITIONS = {"matsubara": MATSUBARA, "pade": PADE}
@@ -220,6 +220,10 @@ class Run:
         self.N = int(np.asarray(system.H).shape[0])
         self.n_ado = self.hier.n_ado
         self.record_len = int(L.heom_record_len(self._r))
+
+    def layout(self) -> int:
+        """0: ADOs stored as N x N matrices; 1: as their column 0 (coherence block)."""
+        return int(load().heom_run_layout(self._r))
 
     def propagate(self, dt_fs: float, n_steps: int, obs_stride: int = 0):
         _check(load().heom_propagate(self._r, float(dt_fs), int(n_steps), int(obs_stride)))
