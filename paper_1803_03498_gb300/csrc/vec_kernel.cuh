@@ -10,8 +10,9 @@
 //               + sum over the links of u through a mode of state a of R v_a
 // with the link coefficients R of the full form (its column part and diagonal part vanish here).
 // out_u = y_u + ch (L zin)_u as in stage_kernel (Horner RK4).  Lane (a, i) of a warp holds element i
-// of ADO u0 + a (A = floor(32 / N) ADOs per warp); H x goes through warp shuffles, each lane applies
-// the links of its own state (the records of an ADO are ordered by state).
+// of ADO u0 + a (A = floor(32 / N) ADOs per warp); H x goes through warp shuffles.  The links of a
+// chunk are taken 32 records at a time: each lane loads one record and the element of its
+// neighbour, and the products reach the owning lanes by warp shuffles.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -99,18 +100,38 @@ __global__ void __launch_bounds__(kVecWarps * 32) vec_stage_kernel(const __grid_
       const CT f = (CT)c.gsum[u] + term_i;
       rr = fma(-f, x.x, rr);
       ri = fma(-f, x.y, ri);
-      if (li > 0) {  // links of state li: records of ADO u are ordered by state
-        const int64_t lo = c.link_off[u], hi = c.link_off[u + 1];
-        for (int64_t p = lo; p < hi; ++p) {
-          const LinkRec<CT> r = recs[p - rbase];
-          const int s = r.s & kRecStateMask;
-          if (s < li) continue;
-          if (s > li) break;
-          const C2 v = vec_load<N, CT, BT>(c.zin, c.u_split, r.v, li);
-          rr = fma(r.re, v.x, fma(-r.im, v.y, rr));
-          ri = fma(r.re, v.y, fma(r.im, v.x, ri));
+    }
+    // links, 32 records of the chunk at a time: the lane holding a record loads its neighbour's
+    // element s and forms R v_s; the contributions then go to their owner lanes (a, s), a = the
+    // record's ADO in the chunk (tag u mod 32), by a uniform shuffle loop
+    {
+      const int cl = min(cnt, A);
+      const int64_t lo = c.link_off[u0], hi = c.link_off[u0 + cl];
+      for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t t = base + lane;
+        int owner = -1;
+        CT cr = 0, ci = 0;
+        if (t < hi) {
+          const LinkRec<CT> r = recs[t - rbase];
+          const int st = r.s & kRecStateMask;
+          owner = (((r.s >> 8) - u0) & 31) * N + st;
+          const C2 v = vec_load<N, CT, BT>(c.zin, c.u_split, r.v, st);
+          cr = fma(r.re, v.x, -r.im * v.y);
+          ci = fma(r.re, v.y, r.im * v.x);
+        }
+        const int w = (int)min((int64_t)32, hi - base);
+        for (int k = 0; k < w; ++k) {
+          const int o = __shfl_sync(0xffffffffu, owner, k);
+          const CT pr = __shfl_sync(0xffffffffu, cr, k);
+          const CT pi = __shfl_sync(0xffffffffu, ci, k);
+          if (o == lane) {
+            rr += pr;
+            ri += pi;
+          }
         }
       }
+    }
+    if (active) {
       C2 o;
       o.x = has_y ? fma(a.ch, rr, yv.x) : a.ch * rr;
       o.y = has_y ? fma(a.ch, ri, yv.y) : a.ch * ri;
