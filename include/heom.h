@@ -231,14 +231,20 @@ int heom_run_kernel_time(heom_run *r, double *ms, int64_t *launches, double *alg
 
 /*
  * Ragged batches (many independent propagations of different sizes advanced together).
- * heom_batch_create captures steps_per_launch RK4 steps of every run (each run's stage launches on
- * one of up to 32 library-created streams, so small runs execute concurrently; one observable record
- * every obs_stride steps, obs_stride dividing steps_per_launch, 0 = none) into one CUDA graph.  The
+ * heom_batch_create captures steps_per_launch RK4 steps of every run into one CUDA graph (one
+ * observable record every obs_stride steps, obs_stride dividing steps_per_launch, 0 = none).  Small
+ * runs (up to 50,000 ADOs) in the column-0 layout (heom_run_layout 1) of equal n_states and precision
+ * class advance together:
+ * one launch per stage and part (FP64 head, body) covers all of them, with each run's stage
+ * arguments written into its own workspace; such a run's arguments belong to the last batch created
+ * over it, and heom_batch_launch answers HEOM_E_STATE if a run left that layout or joined a later
+ * batch.  Other runs launch per run, on one of up to 32 library-created streams, so small runs
+ * execute concurrently.  The
  * runs must be on the current device, with timing off; the call synchronises their streams first.
  * heom_batch_launch replays the graph n_launches times on a stream of the batch's own (ordered after
  * work already enqueued on every run's stream; later work on a run's stream is ordered after it) and
  * advances each run's step and record counters; HEOM_E_NOMEM if a run's records would overflow
- * max_records.  Results are those of heom_propagate with the same steps (same kernels, same order
+ * max_records.  Results are those of heom_propagate with the same steps (same arithmetic, same order
  * per run).  heom_batch_destroy synchronises the batch's stream and frees the graph (the runs stay).
  * The paper runs independent propagations (rotational averages, polarisation sequences) side by
  * side (section "Distributed memory HEOM implementation"); this is that, on one GPU.

@@ -60,6 +60,8 @@ struct heom_run {
   bool vec = false;                  // every ADO in the coherence block |a><0|: stored as its column 0
   size_t copy_bytes = 0;             // bytes of one state copy (head + body, matrix layout)
   double bytes_full_y = 0, bytes_full_noy = 0, flops_full = 0;  // matrix-layout accounting
+  VecRunDesc *desc_dev = nullptr;    // [8] stage arguments for batched column-0 launches
+  const void *desc_owner = nullptr;  // the batch whose stage arguments desc_dev holds
   std::vector<double> term;          // per state
   double max_rate = 0;               // D * max gamma
   // device
@@ -135,7 +137,7 @@ extern "C" int heom_hier_export(const heom_hier *h, uint8_t *tuples, int32_t *pl
 namespace {
 
 struct Layout {
-  size_t off_loff, off_rh, off_rb, off_gsum, off_rec, off_w, off_cnt;
+  size_t off_loff, off_rh, off_rb, off_gsum, off_rec, off_w, off_cnt, off_desc;
   size_t off_state[3];
   size_t head_bytes, body_bytes;
   size_t total;
@@ -329,6 +331,7 @@ Layout make_layout(int n, const Hierarchy &h, int u_split, int precision, int64_
   L.off_rec = o; o = al(o + (size_t)std::max<int64_t>(max_records, 1) * (n + 5) * sizeof(double));
   L.off_w = o; o = al(o + (size_t)n * sizeof(double));
   L.off_cnt = o; o = al(o + 2 * sizeof(int64_t));  // record counter, device error flag
+  L.off_desc = o; o = al(o + 8 * sizeof(VecRunDesc));  // batched column-0 stage arguments (4 stages x 2)
   L.head_bytes = al((size_t)u_split * E * sizeof(double2));
   L.body_bytes = al((size_t)(n_ado - u_split) * *Ep * be);
   for (int c = 0; c < 3; ++c) {
@@ -602,6 +605,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   r->w_dev = reinterpret_cast<double *>(base + L.off_w);
   r->rec_count = reinterpret_cast<int64_t *>(base + L.off_cnt);
   r->copy_bytes = L.head_bytes + L.body_bytes;
+  r->desc_dev = reinterpret_cast<VecRunDesc *>(base + L.off_desc);
   r->err_dev = reinterpret_cast<int *>(base + L.off_cnt + sizeof(int64_t));
   r->y = view_at(base, L, 0);
   r->zA = view_at(base, L, 1);
@@ -1077,6 +1081,9 @@ __global__ void gather_kernel(StateView src, int Ep, int u_split, int body_fp32,
 }  // namespace heom
 
 // ------------------------------------------------------------------------------------------------
+// runs with more ADOs than this launch per run inside a batch even in the column-0 layout
+static const int64_t kBatchGroupMaxAdos = 50000;
+
 // ragged batches: the stage launches of many runs, each on one of a pool of streams, captured into
 // one CUDA graph that advances every run by steps_per_launch RK4 steps per replay.
 
@@ -1090,6 +1097,13 @@ struct heom_batch {
   double dt = 0;
   int64_t steps_per_launch = 0, obs_stride = 0;
   std::vector<int64_t> launches_per_replay;
+  // groups of column-0 runs advanced by batched launches: per group its runs, n_states, FP64 or
+  // mixed kernels, stream, and the launch arguments of the 4 stages x {FP64 head, body}
+  std::vector<std::vector<int>> gruns;
+  std::vector<int> gn;
+  std::vector<bool> gfp64;
+  std::vector<cudaStream_t> gstream;
+  std::vector<std::vector<VecBatchArgs>> gargs;
   ~heom_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1138,6 +1152,70 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
     if (e == cudaSuccess) b->ev.push_back(ev);
   }
   if (e != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: streams/events", e); }
+  const double h = dt_fs;
+  // small runs in the column-0 layout: grouped by (n_states, kernel kind); each group advances every stage
+  // of all its runs with one batched launch per part (FP64 head, body), stage arguments in the runs'
+  // workspaces
+  std::vector<std::vector<int>> groups;
+  std::vector<bool> grouped(n_runs, false);
+  for (int i = 0; i < n_runs; ++i) {
+    heom_run *r = b->runs[i];
+    // small runs only: their per-run launches are launch-bound; large runs keep their own launches
+    // (kernel-bound, concurrent on the stream pool)
+    if (!r->vec || r->n_ado > kBatchGroupMaxAdos) continue;
+    bool placed = false;
+    for (auto &gv : groups) {
+      heom_run *q = b->runs[gv[0]];
+      if (q->n == r->n && (q->precision == HEOM_FP64) == (r->precision == HEOM_FP64) && gv.size() < (size_t)kBatchMaxRuns) {
+        gv.push_back(i);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) groups.push_back({i});
+    grouped[i] = true;
+  }
+  int gi = 0;
+  for (const auto &gv : groups) {
+    cudaStream_t gs = b->pool[gi++ % P];
+    const bool fp64 = b->runs[gv[0]]->precision == HEOM_FP64;
+    const int n = b->runs[gv[0]]->n, A = 32 / n;
+    std::vector<VecBatchArgs> ba(8);
+    for (int k = 0; k < 8; ++k) {
+      ba[k].nruns = (int)gv.size();
+      ba[k].chunk0[0] = 0;
+    }
+    for (size_t q = 0; q < gv.size(); ++q) {
+      heom_run *r = b->runs[gv[q]];
+      std::vector<VecRunDesc> hd(8);
+      const StateView zins[4] = {r->y, r->zA, r->zB, r->zA}, outs[4] = {r->zA, r->zB, r->zA, r->y};
+      const double chs[4] = {h / 4, h / 3, h / 2, h};
+      for (int st = 0; st < 4; ++st)
+        for (int part = 0; part < 2; ++part) {
+          VecRunDesc &d = hd[st * 2 + part];
+          std::memset(&d, 0, sizeof(d));
+          d.c = common_for(r, zins[st], r->y, outs[st]);
+          d.c.u_begin = (part == 0 || fp64) ? 0 : r->u_split;
+          d.c.u_end = (part == 0 && !fp64) ? r->u_split : (int)r->n_ado;
+          if (part == 0 && fp64) d.c.u_end = 0;  // FP64 runs: one part
+          d.ch = chs[st];
+          for (int a = 0; a < r->n; ++a)
+            for (int c2 = 0; c2 < r->n; ++c2) d.H[a * kMaxStates + c2] = r->H[a * r->n + c2];
+          for (int a = 0; a < r->n; ++a) d.term[a] = r->term[a];
+          VecBatchArgs &x = ba[st * 2 + part];
+          x.d[q] = r->desc_dev + st * 2 + part;
+          x.chunk0[q + 1] = x.chunk0[q] + (d.c.u_end - d.c.u_begin + A - 1) / A;
+        }
+      cudaError_t ec = cudaMemcpy(r->desc_dev, hd.data(), 8 * sizeof(VecRunDesc), cudaMemcpyHostToDevice);
+      if (ec != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: stage arguments", ec); }
+      r->desc_owner = b;
+    }
+    b->gargs.push_back(std::move(ba));
+    b->gstream.push_back(gs);
+    b->gfp64.push_back(fp64);
+    b->gn.push_back(n);
+    b->gruns.push_back(gv);
+  }
   // wait for everything already enqueued on the runs' own streams, then capture
   for (heom_run *r : b->runs) {
     e = cudaStreamSynchronize(r->stream);
@@ -1149,8 +1227,42 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
   e = cudaEventRecord(b->ev[P], b->origin);
   for (int p = 0; p < P && e == cudaSuccess; ++p) e = cudaStreamWaitEvent(b->pool[p], b->ev[P], 0);
   b->launches_per_replay.assign(n_runs, 0);
-  const double h = dt_fs;
+  // grouped runs: per RK4 step, four stages of batched launches on the group's stream
+  for (size_t g = 0; g < b->gruns.size() && e == cudaSuccess && rc == HEOM_OK; ++g) {
+    const int kind_body = b->gfp64[g] ? 0 : 1;
+    for (int64_t s = 0; s < steps_per_launch && rc == HEOM_OK; ++s) {
+      for (int st = 0; st < 4 && rc == HEOM_OK; ++st) {
+        if (!b->gfp64[g]) {
+          rc = launch_stage_vec_batch(2, b->gn[g], b->gargs[g][st * 2], b->gstream[g], b->runs[0]->sm_count);
+          ++b->launches_per_replay[b->gruns[g][0]];
+        }
+        if (rc == HEOM_OK) {
+          rc = launch_stage_vec_batch(kind_body, b->gn[g], b->gargs[g][st * 2 + 1], b->gstream[g],
+                                      b->runs[0]->sm_count);
+          ++b->launches_per_replay[b->gruns[g][0]];
+        }
+      }
+      if (rc != HEOM_OK) rc = HEOM_E_CUDA;
+      if (rc == HEOM_OK && obs_stride > 0 && (s + 1) % obs_stride == 0) {
+        for (int i : b->gruns[g]) {
+          heom_run *r = b->runs[i];
+          cudaStream_t own = r->stream;
+          const int64_t l0 = r->launches, rec0 = r->records_host, max0 = r->max_records;
+          r->stream = b->gstream[g];
+          r->max_records = INT64_MAX;
+          rc = enqueue_record(r);
+          b->launches_per_replay[i] += r->launches - l0;
+          r->launches = l0;
+          r->records_host = rec0;  // advanced by heom_batch_launch
+          r->max_records = max0;
+          r->stream = own;
+          if (rc != HEOM_OK) break;
+        }
+      }
+    }
+  }
   for (int i = 0; i < n_runs && e == cudaSuccess && rc == HEOM_OK; ++i) {
+    if (grouped[i]) continue;
     heom_run *r = b->runs[i];
     cudaStream_t own = r->stream;
     const int64_t l0 = r->launches, rec0 = r->records_host, max0 = r->max_records;
@@ -1188,6 +1300,12 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
 extern "C" int heom_batch_launch(heom_batch *b, int64_t n_launches) {
   if (!b || n_launches < 0) { set_error("heom_batch_launch: bad arguments"); return HEOM_E_ARG; }
   const int64_t recs = b->obs_stride > 0 ? b->steps_per_launch / b->obs_stride : 0;
+  for (const auto &gv : b->gruns)
+    for (int i : gv)
+      if (!b->runs[i]->vec || b->runs[i]->desc_owner != b) {
+        set_error("heom_batch_launch: a run left the column-0 layout or joined a later batch; create the batch again");
+        return HEOM_E_STATE;
+      }
   for (heom_run *r : b->runs)
     if (r->records_host + recs * n_launches > r->max_records) {
       set_error("heom_batch_launch: observable records of a run would exceed its max_records");

@@ -70,6 +70,22 @@ struct StageCommon {
 int launch_stage_vec(int kind, const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
                      int sm_count);
 
+// Stage arguments of one run for the batched column-0 kernel; lives in the run's workspace.
+struct VecRunDesc {
+  StageCommon c;
+  double ch;
+  double H[kMaxStates * kMaxStates];  // row-major, stride kMaxStates (shifted H, rad/fs)
+  double term[kMaxStates];
+};
+constexpr int kBatchMaxRuns = 1024;   // runs per batched launch (kernel-parameter space)
+struct VecBatchArgs {
+  const VecRunDesc *d[kBatchMaxRuns];
+  int64_t chunk0[kBatchMaxRuns + 1];  // prefix sums of the runs' chunk counts
+  int nruns;
+};
+// One launch of the batched column-0 kernel for runs of n states (kind as launch_stage_vec).
+int launch_stage_vec_batch(int kind, int n, const VecBatchArgs &a, cudaStream_t st, int sm_count);
+
 // Tensor-core (split-TF32) form of the FP32 body stage: Hermitian runs with real H and N <= 16.
 // Returns 1 when it does not cover n_states.
 int launch_stage_tc_a(const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,

@@ -52,99 +52,138 @@ __device__ __forceinline__ typename VCplx<CT>::type vec_load(const StateView &s,
   return r;
 }
 
-// kOwnHead: CT = double, BT = float -- the FP64 head kernel of a mixed-precision run (its own ADOs
-// are in the head region); otherwise the own ADOs are in the body region of storage type BT == CT.
+// One chunk (A = floor(32 / N) consecutive ADOs starting at u0 = c.u_begin + chn A) of the stage
+// out = y + ch L zin.  kOwnHead: CT = double, BT = float -- the FP64 head kernel of a mixed-precision
+// run (its own ADOs are in the head region); otherwise the own ADOs are in the body region of storage
+// type BT == CT.  hrow: row li of H; h00 = H_00; term_i = Delta of state li.
 template <int N, typename CT, typename BT>
-__global__ void __launch_bounds__(kVecWarps * 32) vec_stage_kernel(const __grid_constant__ StageArgs<CT> a) {
+__device__ __forceinline__ void vec_chunk(const StageCommon &c, const CT (&hrow)[N], CT h00, CT term_i, CT ch,
+                                          int chn, int lane) {
   using C2 = typename VCplx<CT>::type;
   constexpr int A = 32 / N;
   constexpr bool kOwnHead = sizeof(CT) == 8 && sizeof(BT) == 4;
+  const int la = lane / N, li = lane - la * N;
+  const bool lane_ok = la < A;
+  const bool has_y = (c.y.head != nullptr) || (c.y.body != nullptr);
+  const LinkRec<CT> *recs = reinterpret_cast<const LinkRec<CT> *>(kOwnHead ? c.recs_head : c.recs_body);
+  const int64_t rbase = kOwnHead ? 0 : c.rec_split;
+  const int u0 = c.u_begin + chn * A;
+  const int cnt = min(A, c.u_end - u0);
+  const bool active = lane_ok && la < cnt;
+  const int64_t u = u0 + la;
+  C2 x;
+  x.x = 0;
+  x.y = 0;
+  C2 yv = x;
+  if (active) {
+    x = vec_load<N, CT, BT>(c.zin, c.u_split, u, li);
+    if (has_y) yv = vec_load<N, CT, BT>(c.y, c.u_split, u, li);
+  }
+  // -i (H x)_i + i H_00 x_i
+  CT rr = -h00 * x.y, ri = h00 * x.x;
+#pragma unroll
+  for (int b = 0; b < N; ++b) {
+    const CT xr = __shfl_sync(0xffffffffu, x.x, min(la, A - 1) * N + b);
+    const CT xi = __shfl_sync(0xffffffffu, x.y, min(la, A - 1) * N + b);
+    rr = fma(hrow[b], xi, rr);
+    ri = fma(-hrow[b], xr, ri);
+  }
+  if (active) {
+    const CT f = (CT)c.gsum[u] + term_i;
+    rr = fma(-f, x.x, rr);
+    ri = fma(-f, x.y, ri);
+  }
+  // links, 32 records of the chunk at a time: the lane holding a record loads its neighbour's
+  // element s and forms R v_s; the contributions then go to their owner lanes (a, s), a = the
+  // record's ADO in the chunk (tag u mod 32), by a uniform shuffle loop
+  {
+    const int64_t lo = c.link_off[u0], hi = c.link_off[u0 + cnt];
+    for (int64_t base = lo; base < hi; base += 32) {
+      const int64_t t = base + lane;
+      int owner = -1;
+      CT cr = 0, ci = 0;
+      if (t < hi) {
+        const LinkRec<CT> r = recs[t - rbase];
+        const int st = r.s & kRecStateMask;
+        owner = (((r.s >> 8) - u0) & 31) * N + st;
+        const C2 v = vec_load<N, CT, BT>(c.zin, c.u_split, r.v, st);
+        cr = fma(r.re, v.x, -r.im * v.y);
+        ci = fma(r.re, v.y, r.im * v.x);
+      }
+      const int w = (int)min((int64_t)32, hi - base);
+      for (int k = 0; k < w; ++k) {
+        const int o = __shfl_sync(0xffffffffu, owner, k);
+        const CT pr = __shfl_sync(0xffffffffu, cr, k);
+        const CT pi = __shfl_sync(0xffffffffu, ci, k);
+        if (o == lane) {
+          rr += pr;
+          ri += pi;
+        }
+      }
+    }
+  }
+  if (active) {
+    C2 o;
+    o.x = has_y ? fma(ch, rr, yv.x) : ch * rr;
+    o.y = has_y ? fma(ch, ri, yv.y) : ch * ri;
+    if (kOwnHead || u < c.u_split) {
+      c.out.head[u * N + li] = make_double2((double)o.x, (double)o.y);
+    } else {
+      typename VCplx<BT>::type w;
+      w.x = (BT)o.x;
+      w.y = (BT)o.y;
+      reinterpret_cast<typename VCplx<BT>::type *>(c.out.body)[(u - c.u_split) * N + li] = w;
+    }
+  }
+}
+
+template <int N, typename CT, typename BT>
+__global__ void __launch_bounds__(kVecWarps * 32) vec_stage_kernel(const __grid_constant__ StageArgs<CT> a) {
+  constexpr int A = 32 / N;
   const StageCommon &c = a.c;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kVecWarps + (threadIdx.x >> 5);
   const int nw = gridDim.x * kVecWarps;
   const int la = lane / N, li = lane - la * N;
   const bool lane_ok = la < A;
-  const bool has_y = (c.y.head != nullptr) || (c.y.body != nullptr);
-  const LinkRec<CT> *recs = reinterpret_cast<const LinkRec<CT> *>(kOwnHead ? c.recs_head : c.recs_body);
-  const int64_t rbase = kOwnHead ? 0 : c.rec_split;
   CT hrow[N];
 #pragma unroll
   for (int b = 0; b < N; ++b) hrow[b] = lane_ok ? a.H[li * kMaxStates + b] : (CT)0;
   const CT h00 = a.H[0];
   const CT term_i = lane_ok ? a.term[li] : (CT)0;
   const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
-  for (int chn = gw; chn < n_chunks; chn += nw) {
-    const int u0 = c.u_begin + chn * A;
-    const int cnt = min(A, c.u_end - u0);
-    const bool active = lane_ok && la < cnt;
-    const int64_t u = u0 + la;
-    C2 x;
-    x.x = 0;
-    x.y = 0;
-    C2 yv = x;
-    if (active) {
-      x = vec_load<N, CT, BT>(c.zin, c.u_split, u, li);
-      if (has_y) yv = vec_load<N, CT, BT>(c.y, c.u_split, u, li);
+  for (int chn = gw; chn < n_chunks; chn += nw) vec_chunk<N, CT, BT>(c, hrow, h00, term_i, a.ch, chn, lane);
+}
+
+// Many runs of the same N in one launch (ragged batches): run k's chunks are the launch's chunks
+// [chunk0[k], chunk0[k+1]); its stage arguments sit in its own workspace (d[k]).
+template <int N, typename CT, typename BT>
+__global__ void __launch_bounds__(kVecWarps * 32) vec_batch_kernel(const __grid_constant__ VecBatchArgs a) {
+  constexpr int A = 32 / N;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kVecWarps + (threadIdx.x >> 5);
+  const int nw = gridDim.x * kVecWarps;
+  const int la = lane / N, li = lane - la * N;
+  const bool lane_ok = la < A;
+  const int64_t total = a.chunk0[a.nruns];
+  int k = 0;
+  for (int64_t g = gw; g < total; g += nw) {
+    int lo = 0, hi = a.nruns - 1;  // the run holding global chunk g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.chunk0[mid] <= g) lo = mid;
+      else hi = mid - 1;
     }
-    // -i (H x)_i + i H_00 x_i
-    CT rr = -h00 * x.y, ri = h00 * x.x;
+    k = lo;
+    const VecRunDesc *d = a.d[k];
+    const StageCommon c = d->c;  // by value: registers, not reloads after the chunk's stores
+    CT hrow[N];
 #pragma unroll
-    for (int b = 0; b < N; ++b) {
-      const CT xr = __shfl_sync(0xffffffffu, x.x, min(la, A - 1) * N + b);
-      const CT xi = __shfl_sync(0xffffffffu, x.y, min(la, A - 1) * N + b);
-      rr = fma(hrow[b], xi, rr);
-      ri = fma(-hrow[b], xr, ri);
-    }
-    if (active) {
-      const CT f = (CT)c.gsum[u] + term_i;
-      rr = fma(-f, x.x, rr);
-      ri = fma(-f, x.y, ri);
-    }
-    // links, 32 records of the chunk at a time: the lane holding a record loads its neighbour's
-    // element s and forms R v_s; the contributions then go to their owner lanes (a, s), a = the
-    // record's ADO in the chunk (tag u mod 32), by a uniform shuffle loop
-    {
-      const int cl = min(cnt, A);
-      const int64_t lo = c.link_off[u0], hi = c.link_off[u0 + cl];
-      for (int64_t base = lo; base < hi; base += 32) {
-        const int64_t t = base + lane;
-        int owner = -1;
-        CT cr = 0, ci = 0;
-        if (t < hi) {
-          const LinkRec<CT> r = recs[t - rbase];
-          const int st = r.s & kRecStateMask;
-          owner = (((r.s >> 8) - u0) & 31) * N + st;
-          const C2 v = vec_load<N, CT, BT>(c.zin, c.u_split, r.v, st);
-          cr = fma(r.re, v.x, -r.im * v.y);
-          ci = fma(r.re, v.y, r.im * v.x);
-        }
-        const int w = (int)min((int64_t)32, hi - base);
-        for (int k = 0; k < w; ++k) {
-          const int o = __shfl_sync(0xffffffffu, owner, k);
-          const CT pr = __shfl_sync(0xffffffffu, cr, k);
-          const CT pi = __shfl_sync(0xffffffffu, ci, k);
-          if (o == lane) {
-            rr += pr;
-            ri += pi;
-          }
-        }
-      }
-    }
-    if (active) {
-      C2 o;
-      o.x = has_y ? fma(a.ch, rr, yv.x) : a.ch * rr;
-      o.y = has_y ? fma(a.ch, ri, yv.y) : a.ch * ri;
-      if (kOwnHead || u < c.u_split) {
-        c.out.head[u * N + li] = make_double2((double)o.x, (double)o.y);
-      } else {
-        typename VCplx<BT>::type w;
-        w.x = (BT)o.x;
-        w.y = (BT)o.y;
-        reinterpret_cast<typename VCplx<BT>::type *>(c.out.body)[(u - c.u_split) * N + li] = w;
-      }
-    }
+    for (int b = 0; b < N; ++b) hrow[b] = lane_ok ? (CT)__ldg(&d->H[li * kMaxStates + b]) : (CT)0;
+    const CT h00 = (CT)__ldg(&d->H[0]), term_i = lane_ok ? (CT)__ldg(&d->term[li]) : (CT)0;
+    vec_chunk<N, CT, BT>(c, hrow, h00, term_i, (CT)__ldg(&d->ch), (int)(g - a.chunk0[k]), lane);
   }
+  (void)k;
 }
 
 template <int N, typename CT, typename BT>
@@ -177,6 +216,30 @@ int launch_vec_n(const StageCommon &c, double ch, const double *term, const doub
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("vector stage kernel launch: ") + cudaGetErrorString(e));
+    return -4;
+  }
+  return 0;
+}
+
+template <int N, typename CT, typename BT>
+int launch_vec_batch_n(const VecBatchArgs &a, cudaStream_t st, int sm_count) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int ps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, vec_batch_kernel<N, CT, BT>, kVecWarps * 32, 0);
+    if (e != cudaSuccess || ps < 1) {
+      set_error(std::string("batched vector kernel: occupancy query failed: ") + cudaGetErrorString(e));
+      return -4;
+    }
+    per_sm = ps;
+  }
+  const int64_t total = a.chunk0[a.nruns];
+  if (total <= 0) return 0;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + kVecWarps - 1) / kVecWarps, (int64_t)per_sm * sm_count));
+  vec_batch_kernel<N, CT, BT><<<grid, kVecWarps * 32, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("batched vector kernel launch: ") + cudaGetErrorString(e));
     return -4;
   }
   return 0;

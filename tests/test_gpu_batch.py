@@ -76,3 +76,29 @@ def test_batch_argument_errors(heom):
         b.launch(2)                       # 4 more records, room for 2
     assert ei.value.code == heom.HEOM_E_NOMEM
     b.close()
+
+
+def test_grouped_runs_guard_their_stage_arguments(heom):
+    """Column-0 runs of a batch share batched launches whose stage arguments live in the runs'
+    workspaces: a run that joins a later batch, or leaves the column-0 layout, makes the earlier batch
+    refuse to launch (HEOM_E_STATE) instead of computing with stale arguments."""
+    props = [p for p in wl.ragged_batch(n_systems=4, n_steps=10)][:6]
+    runs = make_runs(heom, props, "fp32_mixed", 10, 5)
+    assert all(r.layout() == 1 for r in runs)
+    b1 = heom.Batch(runs, 0.5, 5, 5)
+    b1.launch(1)
+    b2 = heom.Batch(runs[:2], 0.25, 5, 5)
+    with pytest.raises(heom.HeomError) as ei:
+        b1.launch(1)
+    assert ei.value.code == heom.HEOM_E_STATE
+    b2.launch(1)
+    b3 = heom.Batch(runs, 0.5, 5, 5)
+    re, im = runs[3].get_ados(0, 1)
+    re[0, 0, 1] = 0.5  # outside column 0
+    runs[3].set_ados(0, re, im)
+    assert runs[3].layout() == 0
+    with pytest.raises(heom.HeomError) as ei:
+        b3.launch(1)
+    assert ei.value.code == heom.HEOM_E_STATE
+    for b in (b1, b2, b3):
+        b.close()
