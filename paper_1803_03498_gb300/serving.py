@@ -197,3 +197,33 @@ class Server:
                     time.sleep(0.0002)
         stats = ServeStats(results=[results[k] for k in sorted(results)], wall_s=now())
         return stats
+
+
+def main(argv=None):
+    """Rate sweep of the serving loop on seeded Poisson streams (one JSON line per offered rate)."""
+    import argparse
+    import json
+
+    from . import heom
+    from . import workloads as wl
+
+    ap = argparse.ArgumentParser(prog="python -m paper_1803_03498_gb300.serving")
+    ap.add_argument("--rates", type=float, nargs="+", default=[5, 10, 20, 50, 100, 200])
+    ap.add_argument("--requests", type=int, default=500)
+    ap.add_argument("--max-ado-steps", type=float, default=2e7,
+                    help="redraw requests above this ADOs x steps (a bounded sample of the mix)")
+    ap.add_argument("--budget", type=float, default=120e9)
+    ap.add_argument("--precision", default="fp32_mixed")
+    args = ap.parse_args(argv)
+    heom.load()
+    for rate in args.rates:
+        reqs = wl.serving_stream(rate, args.requests, max_ado_steps=args.max_ado_steps)
+        st = Server(budget_bytes=args.budget, precision=args.precision).serve(reqs, real_time=True)
+        s = st.summary()
+        s.update({"offered_rate_req_per_s": rate, "max_ado_steps": args.max_ado_steps, "precision": args.precision})
+        print(json.dumps(s), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
