@@ -5,7 +5,8 @@ A request is one propagation (system, rho(0), dt, steps).  The server
   * admits arrived requests first-fit while their device workspace (heom_run_bytes) fits the remaining
     memory budget; a request larger than the whole budget is rejected at once (it can never run);
   * gives every admitted request its own CUDA stream and advances it by `quantum` RK4 steps at a time
-    (one replay of a CUDA graph captured at admission, so a quantum costs one launch on the host), so
+    (replays of a CUDA graph of `graph_steps` steps captured at admission, by default the whole
+    quantum: one launch on the host per quantum), so
     the work of all admitted requests overlaps on the device, and requests that arrive while others
     are running are admitted as soon as memory frees up (no batch boundary: continuous batching);
   * on completion copies the observables back, frees the workspace and records the latency
@@ -81,15 +82,20 @@ class ServeStats:
 
 class Server:
     def __init__(self, budget_bytes: float = 120e9, precision: str = "fp32_mixed", quantum: int = 100,
-                 max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False):
+                 max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False, graph_steps: int | None = None):
         if obs_stride > 0 and quantum % obs_stride:
             raise ValueError("obs_stride must divide quantum")
+        if graph_steps is None:  # one graph per quantum (measured: fewer, longer graphs serve more)
+            graph_steps = quantum
+        if graph_steps < 1 or quantum % graph_steps or (obs_stride > 0 and graph_steps % obs_stride):
+            raise ValueError("graph_steps must divide quantum and be a multiple of obs_stride")
         self.budget = int(budget_bytes)
         self.precision = precision
         self.quantum = int(quantum)
         self.max_active = int(max_active)
         self.obs_stride = int(obs_stride)
         self.keep_sigma0 = keep_sigma0
+        self.graph_steps = int(graph_steps)
         self._hier_cache = {}
 
     def _hier(self, heom, M, D):
@@ -154,7 +160,7 @@ class Server:
                     res.admitted_s = now()
                     graph = None
                     if r.prop.n_steps >= self.quantum:
-                        graph = heom.Batch([run], r.prop.dt_fs, self.quantum, self.obs_stride)
+                        graph = heom.Batch([run], r.prop.dt_fs, self.graph_steps, self.obs_stride)
                     ev = torch.cuda.Event()
                     ev.record(st)
                     active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph))
@@ -169,7 +175,7 @@ class Server:
                 if a.remaining > 0:
                     st = streams[a.stream]
                     if a.graph is not None and a.remaining >= self.quantum:
-                        a.graph.launch(1)
+                        a.graph.launch(self.quantum // self.graph_steps)
                         q = self.quantum
                     else:
                         q = a.remaining
