@@ -148,7 +148,10 @@ int heom_run_bytes(const heom_system *sys, const heom_hier *h, int precision, in
  * sum_a w_a sigma_0[a][0] recorded with every observable record (Eq. lin_abs_mukamel with
  * sigma_0(0) = mu^+|0><0|, state 0 the ground state).  Errors: HEOM_E_ARG, HEOM_E_NOMEM
  * (workspace too small), HEOM_E_CUDA.  The workspace must stay allocated until
- * heom_run_destroy.
+ * heom_run_destroy.  Mixed-precision runs also own one library stream and two events: each stage's
+ * small FP64 head launch runs there, forked from and joined back into the caller's stream, so that
+ * it overlaps the body launch (work enqueued on the caller's stream stays ordered).  The bath
+ * coefficients follow sys->decomposition (Matsubara or Pade).
  */
 int heom_run_create(const heom_system *sys, const heom_hier *h, int precision, int64_t max_records,
                     const double *sigma0_re, const double *sigma0_im, const double *dip_w,

@@ -52,6 +52,8 @@ struct heom_run {
   int u_split = 0;                   // ADOs stored in FP64 in the head region
   int E = 0, Ep = 0;                 // tile size, body tile pitch
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;       // library stream for the FP64 head launches (they overlap the body)
+  cudaEvent_t fork = nullptr, join = nullptr;
   int sm_count = 0;
   // host copies of the per-run constants (rad/fs)
   std::vector<double> H, Hi;         // shifted Re H, Im H
@@ -89,6 +91,9 @@ struct heom_run {
   double flops_gen = 0, flops_herm = 0;             // per launch: general and Hermitian forms
   ~heom_run() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
   }
 };
 
@@ -444,7 +449,12 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&r->sm_count, cudaDevAttrMultiProcessorCount, dev);
-  if (ce != cudaSuccess) { delete r; return cuda_fail("device query", ce); }
+  if (ce == cudaSuccess && r->u_split > 0) {  // the FP64 head launches run beside the body launches
+    ce = cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming);
+  }
+  if (ce != cudaSuccess) { delete r; return cuda_fail("device query / head stream", ce); }
 
   // ---- units and Hamiltonian: H in rad/fs, shifted by h0 = (max + min)/2 of Re diag (exact for
   // the commutator, the only place H enters) to keep the products small in FP32.
@@ -696,6 +706,22 @@ static int timed_end(heom_run *r, double bytes) {
   return HEOM_OK;
 }
 
+// The FP64 head launch of a mixed-precision stage goes to the run's side stream, forked from and
+// joined back into the run's stream (capturable), so that it overlaps the body launch: both read zin
+// and write disjoint parts of out.
+static cudaStream_t fork_head(heom_run *r) {
+  if (!r->side) return r->stream;
+  if (cudaEventRecord(r->fork, r->stream) != cudaSuccess || cudaStreamWaitEvent(r->side, r->fork, 0) != cudaSuccess)
+    return r->stream;
+  return r->side;
+}
+static int join_head(heom_run *r, cudaStream_t hs) {
+  if (hs == r->stream) return HEOM_OK;
+  cudaError_t e = cudaEventRecord(r->join, hs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(r->stream, r->join, 0);
+  return e == cudaSuccess ? HEOM_OK : cuda_fail("head stream join", e);
+}
+
 static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, double ch) {
   StageCommon c = common_for(r, zin, y, out);
   const double *Hi = r->cplx_h ? r->Hi.data() : nullptr;
@@ -703,22 +729,26 @@ static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, dou
   const bool same_y = (y.head == zin.head && y.body == zin.body);
   const bool no_y = (y.head == nullptr && y.body == nullptr);
   if (r->vec) {  // coherence block: column-0 kernels
+    cudaStream_t hs = r->stream;
     if (r->precision != HEOM_FP64) {
       c.u_begin = 0;
       c.u_end = r->u_split;
-      rc = launch_stage_vec(2, c, ch, r->term.data(), r->H.data(), r->stream, r->sm_count);
+      hs = fork_head(r);
+      rc = launch_stage_vec(2, c, ch, r->term.data(), r->H.data(), hs, r->sm_count);
       if (rc) return HEOM_E_CUDA;
       ++r->launches;
     }
     c.u_begin = (r->precision == HEOM_FP64) ? 0 : r->u_split;
     c.u_end = (int)r->n_ado;
-    if (c.u_end <= c.u_begin) return HEOM_OK;
-    if ((rc = timed_begin(r))) return rc;
-    rc = launch_stage_vec(r->precision == HEOM_FP64 ? 0 : 1, c, ch, r->term.data(), r->H.data(), r->stream,
-                          r->sm_count);
-    if (rc) return HEOM_E_CUDA;
-    ++r->launches;
-    return timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y);
+    if (c.u_end > c.u_begin) {
+      if ((rc = timed_begin(r))) return rc;
+      rc = launch_stage_vec(r->precision == HEOM_FP64 ? 0 : 1, c, ch, r->term.data(), r->H.data(), r->stream,
+                            r->sm_count);
+      if (rc) return HEOM_E_CUDA;
+      ++r->launches;
+      if ((rc = timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y))) return rc;
+    }
+    return join_head(r, hs);
   }
   if (r->precision == HEOM_FP64) {
     c.u_begin = 0;
@@ -729,10 +759,11 @@ static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, dou
     ++r->launches;
     return timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y);
   }
-  // mixed: FP64 head (levels 0, 1) and FP32 body
+  // mixed: FP64 head (levels 0, 1, on the side stream) and FP32 body
   c.u_begin = 0;
   c.u_end = r->u_split;
-  rc = launch_stage(2, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
+  const cudaStream_t hs = fork_head(r);
+  rc = launch_stage(2, c, ch, r->term.data(), r->H.data(), Hi, hs, r->sm_count);
   if (rc) return HEOM_E_CUDA;
   ++r->launches;
   c.u_begin = r->u_split;
@@ -747,9 +778,9 @@ static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, dou
     if (rc == 1) rc = launch_stage(1, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
     if (rc) return HEOM_E_CUDA;
     ++r->launches;
-    return timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y);
+    if ((rc = timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y))) return rc;
   }
-  return HEOM_OK;
+  return join_head(r, hs);
 }
 
 extern "C" int heom_run_set_timing(heom_run *r, int enable) {
@@ -1015,13 +1046,14 @@ __device__ __forceinline__ double2 ld_elem(const StateView &s, int n, int Ep, in
 // One observable record of sigma_0 (FP64): populations, trace, dipole correlation, Hermiticity.
 __global__ void record_kernel(StateView y, int u_split, int body_fp32, int vec, int n, const double *w, double *records,
                               int64_t *rec_count, int64_t max_records) {
-  if (threadIdx.x != 0) return;
+  // one warp: lane a handles rows a, a + 32, ...; sums and the maximum are reduced across the warp
+  const int lane = threadIdx.x & 31;
   const int64_t idx = *rec_count;
   if (idx >= max_records) return;
   const int E = n * n;
   double *rec = records + idx * (n + 5);
   double tr = 0, ti = 0, cr = 0, ci = 0, herm = 0;
-  for (int a = 0; a < n; ++a) {
+  for (int a = lane; a < n; a += 32) {
     const double2 d = ld_elem(y, n, E, u_split, body_fp32, vec, 0, (int64_t)a * n + a);
     rec[a] = d.x;
     tr += d.x;
@@ -1035,12 +1067,21 @@ __global__ void record_kernel(StateView y, int u_split, int body_fp32, int vec, 
       herm = fmax(herm, hypot(x.x - z.x, x.y + z.y));
     }
   }
-  rec[n] = tr;
-  rec[n + 1] = ti;
-  rec[n + 2] = cr;
-  rec[n + 3] = ci;
-  rec[n + 4] = herm;
-  *rec_count = idx + 1;
+  for (int o = 16; o > 0; o >>= 1) {
+    tr += __shfl_down_sync(0xffffffffu, tr, o);
+    ti += __shfl_down_sync(0xffffffffu, ti, o);
+    cr += __shfl_down_sync(0xffffffffu, cr, o);
+    ci += __shfl_down_sync(0xffffffffu, ci, o);
+    herm = fmax(herm, __shfl_down_sync(0xffffffffu, herm, o));
+  }
+  if (lane == 0) {
+    rec[n] = tr;
+    rec[n + 1] = ti;
+    rec[n + 2] = cr;
+    rec[n + 3] = ci;
+    rec[n + 4] = herm;
+    *rec_count = idx + 1;
+  }
 }
 
 __global__ void scatter_kernel(StateView dst, int Ep, int u_split, int body_fp32, int vec, int n, int64_t u0, int64_t count,
