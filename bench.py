@@ -202,7 +202,8 @@ def time_e2e(prop, precision, steps, hier):
 def time_batch(steps=20, per_launch=10):
     """The ragged batch (64 systems x 3 dipole orientations = 192 runs, N+1 in 3..17, D in 3..5,
     K in 0..1, mixed precision): all runs in one CUDA graph per `per_launch` steps, against the same
-    runs propagated one after another with heom_propagate.  Returns a dict."""
+    runs propagated one after another with heom_propagate.  Dipole runs take the column-0 layout.
+    Returns a dict."""
     import torch
 
     from paper_1803_03498_gb300 import heom
@@ -225,6 +226,7 @@ def time_batch(steps=20, per_launch=10):
     e1.record(st)
     torch.cuda.synchronize()
     ms_batch = e0.elapsed_time(e1)
+    runs_layout = list(runs)
     # sequential: one run after the other, each run's steps enqueued as separate launches
     for r in runs:
         r.propagate(dt, 1, 0)
@@ -242,7 +244,10 @@ def time_batch(steps=20, per_launch=10):
                         "N+1 in 3..17, D in 3..5, K in 0..1, fp32_mixed, dt=0.5 fs",
             "value": evals / (ms_batch / 1000), "unit": UNIT, "steps": steps, "ms_per_step": ms_batch / steps,
             "sequential_value": evals / (ms_seq / 1000), "speedup_vs_sequential": ms_seq / ms_batch,
-            "graph": f"one CUDA graph per {per_launch} steps of all runs (capture + instantiate {t_capture:.2f} s)"}
+            "layout": "every run in the column-0 (coherence-block) layout" if all(r_.layout() == 1 for r_ in runs_layout)
+                      else "mixed layouts",
+            "graph": f"one CUDA graph per {per_launch} steps of all runs: runs up to 50,000 ADOs grouped by N into "
+                     f"one launch per stage, larger runs one launch each (capture + instantiate {t_capture:.2f} s)"}
 
 
 def time_serving(rates=(5.0, 20.0), n_requests=60, max_ado_steps=2e7, budget=120e9):
