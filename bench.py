@@ -226,7 +226,8 @@ def time_batch(steps=20, per_launch=10):
     e1.record(st)
     torch.cuda.synchronize()
     ms_batch = e0.elapsed_time(e1)
-    runs_layout = list(runs)
+    layout = ("every run in the column-0 (coherence-block) layout" if all(r.layout() == 1 for r in runs)
+              else "mixed layouts")
     # sequential: one run after the other, each run's steps enqueued as separate launches
     for r in runs:
         r.propagate(dt, 1, 0)
@@ -244,8 +245,7 @@ def time_batch(steps=20, per_launch=10):
                         "N+1 in 3..17, D in 3..5, K in 0..1, fp32_mixed, dt=0.5 fs",
             "value": evals / (ms_batch / 1000), "unit": UNIT, "steps": steps, "ms_per_step": ms_batch / steps,
             "sequential_value": evals / (ms_seq / 1000), "speedup_vs_sequential": ms_seq / ms_batch,
-            "layout": "every run in the column-0 (coherence-block) layout" if all(r_.layout() == 1 for r_ in runs_layout)
-                      else "mixed layouts",
+            "layout": layout,
             "graph": f"one CUDA graph per {per_launch} steps of all runs: runs up to 50,000 ADOs grouped by N into "
                      f"one launch per stage, larger runs one launch each (capture + instantiate {t_capture:.2f} s)"}
 
