@@ -173,6 +173,10 @@ def time_gpu(prop, precision, steps, warmup, ws, clocks=None):
     launches = run.launches() - l0
     kt = run.kernel_time()
     obs = run.observables()
+    # the launch schedules the autotuner picked at run creation (occupancy %, chunks per warp)
+    kt["schedule"] = {"body": list(run.schedule(0))}
+    if precision != "fp64":
+        kt["schedule"]["head"] = list(run.schedule(1))
     run.close()
     return ms, launches, kt, obs, clk
 
@@ -228,6 +232,10 @@ def time_batch(steps=20, per_launch=10):
     ms_batch = e0.elapsed_time(e1)
     layout = ("every run in the column-0 (coherence-block) layout" if all(r.layout() == 1 for r in runs)
               else "mixed layouts")
+    sched = {}
+    for body, head in b.schedules():  # per group of batched launches: what the autotuner picked
+        key = f"body {body[0]}% x{body[1]} chunks, head {head[0]}% x{head[1]} chunks"
+        sched[key] = sched.get(key, 0) + 1
     # sequential: one run after the other, each run's steps enqueued as separate launches
     for r in runs:
         r.propagate(dt, 1, 0)
@@ -246,8 +254,10 @@ def time_batch(steps=20, per_launch=10):
             "value": evals / (ms_batch / 1000), "unit": UNIT, "steps": steps, "ms_per_step": ms_batch / steps,
             "sequential_value": evals / (ms_seq / 1000), "speedup_vs_sequential": ms_seq / ms_batch,
             "layout": layout,
+            "group_schedules": sched,
             "graph": f"one CUDA graph per {per_launch} steps of all runs: runs up to 50,000 ADOs grouped by N into "
-                     f"one launch per stage, larger runs one launch each (capture + instantiate {t_capture:.2f} s)"}
+                     f"one launch per stage, larger runs one launch each (autotune + capture + instantiate "
+                     f"{t_capture:.2f} s)"}
 
 
 def time_serving(rates=(5.0, 20.0), n_requests=60, max_ado_steps=2e7, budget=120e9):
@@ -449,19 +459,22 @@ def main():
                          "frac_per_unit_4_tiles": unit4 / (kt["ms"] / max(kt["launches"], 1) / 1000.0) / 1e9 / hbm_peak,
                          "kernel": "stage_kernel<14,float,float> (levels >= 2)",
                          "peak_source": peak_src, "timed_launches": kt["launches"],
-                         "avg_launch_ms": kt["ms"] / max(kt["launches"], 1)},
+                         "avg_launch_ms": kt["ms"] / max(kt["launches"], 1),
+                         "schedule": kt["schedule"]},
             "fp64": {"value": v64, "unit": UNIT, "steps": f64_steps, "ms_per_step": ms64 / f64_steps,
                      "mixed_over_fp64": value / v64,
                      "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                   "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": traffic64,
                                   "kernel": "stage_kernel<14,double,double>",
-                                  "avg_launch_ms": kt64["ms"] / max(kt64["launches"], 1)}},
+                                  "avg_launch_ms": kt64["ms"] / max(kt64["launches"], 1),
+                                  "schedule": kt64["schedule"]}},
             "split_tf32": {"value": v_tc, "unit": UNIT, "steps": tc_steps, "ms_per_step": ms_tc / tc_steps,
                            "pop_diff_vs_fp64": pop_diff_tc,
                            "roofline": {"bound": "hbm", "achieved": ach_tc, "peak": hbm_peak, "unit": "GB/s",
                                         "frac": ach_tc / hbm_peak, "traffic": None,
                                         "kernel": "stage_tc_kernel<14> (tcgen05.mma kind::tf32, levels >= 2)",
-                                        "avg_launch_ms": kt_tc["ms"] / max(kt_tc["launches"], 1)}},
+                                        "avg_launch_ms": kt_tc["ms"] / max(kt_tc["launches"], 1),
+                                        "schedule": kt_tc["schedule"]}},
             "mixed_vs_fp64_pop_diff": pop_diff,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "what": "heom_run_create from host arrays + propagate + observables to host, wall clock"},

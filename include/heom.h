@@ -259,6 +259,62 @@ int heom_batch_launch(heom_batch *b, int64_t n_launches);
 int heom_batch_destroy(heom_batch *b);
 
 /*
+ * Launch schedules and the autotuner (not in the paper, whose kernels are fixed; the choices below
+ * map the same arithmetic onto the GPU differently).  A stage launch covers its ADOs in chunks of
+ * floor(32 / n_states) consecutive ADOs over a persistent grid of CTAs.  A schedule fixes what the
+ * arithmetic leaves open:
+ *   occupancy_pct     1..100: the grid is sized for this percentage of the kernel's CTAs that fit
+ *                     on one SM (rounded down, at least 1) times the SM count;
+ *   chunks_per_warp   1, 2 or 4: column-0 kernels (heom_run_layout 1) let each warp hold this many
+ *                     consecutive chunks at once (capped at 32 ADOs per warp: 2 for n_states 2, 3
+ *                     for 3), one element of each per lane, and load the link records and
+ *                     neighbour elements of all of them together, so that their memory round trips
+ *                     overlap (more registers per thread).  Matrix-layout kernels ignore it.
+ * Every schedule gives bit-identical results: each output element sums the same terms in the same
+ * order.  Only the time differs.  The default is {100, 1}.
+ *
+ * heom_schedule_candidates -- host only: the candidates the tuner times for a layout (0 matrix,
+ *   1 column-0 run, 2 column-0 batch group) into out[cap]; returns their number (or a negative
+ *   status).
+ * heom_tune -- times every candidate of one part of a run (part 0: the body, the stage kernel over
+ *   the bulk of the hierarchy; part 1: the FP64 head launch of a mixed-precision run) on the run's
+ *   own stage-1 launch (reads the state, writes an intermediate copy: the state is unchanged),
+ *   one warm-up and reps timed launches each, on the run's stream, and keeps the fastest for the
+ *   run and in a process-wide cache keyed by (layout, precision, part, n_states, Hermitian,
+ *   complex H, floor(log2 of the part's ADO count)).  Outputs (caller-owned, may be NULL):
+ *   tried[cap] and ms[cap] (mean ms per launch, in candidate order), *n_tried, *chosen.
+ *   Synchronises the stream.  HEOM_E_ARG: reps < 1, part not 0/1, part 1 of a run without a head;
+ *   HEOM_E_STATE: the run's stream is being captured.
+ * heom_set_autotune -- process-wide.  reps > 0: heom_run_create and heom_batch_create tune every
+ *   part whose cache key has no entry yet (reps timed launches per candidate), and take cached
+ *   entries otherwise; 0: no tuning at creation (cached entries still apply; other parts take the
+ *   layout's default schedule, below).  Returns the previous value; a negative argument only queries.  Default 3.
+ *   heom_propagate_static never tunes.
+ * heom_get_schedule / heom_set_schedule -- the schedule a part of a run launches with; set checks
+ *   the ranges above (HEOM_E_ARG) and does not touch the cache.
+ * heom_set_default_schedule -- the schedule that parts of a layout (0, 1, 2 as above) take when the
+ *   cache has no entry and no tuning runs; NULL restores {100, 1}.  Applies to later creations.
+ * heom_tune_cache_clear -- empties the cache.
+ * heom_batch_schedule -- the schedule of part (0 body, 1 FP64 head) of group g of a batch's
+ *   grouped column-0 launches (tuned at heom_batch_create under autotuning, layout 2 in the cache
+ *   key, with the group's total ADO count); *n_groups gets the number of groups (g may then be
+ *   -1 to query only that).
+ */
+typedef struct {
+  int occupancy_pct;
+  int chunks_per_warp;
+} heom_schedule;
+int heom_schedule_candidates(int layout, heom_schedule *out, int cap);
+int heom_tune(heom_run *r, int part, int reps, heom_schedule *tried, double *ms, int cap, int *n_tried,
+              heom_schedule *chosen);
+int heom_set_autotune(int reps);
+int heom_get_schedule(const heom_run *r, int part, heom_schedule *out);
+int heom_set_schedule(heom_run *r, int part, const heom_schedule *s);
+int heom_set_default_schedule(int layout, const heom_schedule *s);
+int heom_tune_cache_clear(void);
+int heom_batch_schedule(const heom_batch *b, int g, int part, heom_schedule *out, int *n_groups);
+
+/*
  * heom_propagate_static -- one complete propagation that allocates no device memory, for callers
  * that cannot call cudaMalloc (code running while its stream is being captured into a CUDA graph,
  * plug-ins whose host application owns every device allocation, latency-critical paths that cannot

@@ -3,8 +3,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -32,6 +36,26 @@ int launch_stage(int precision, const StageCommon &c, double ch, const double *t
   }
   return rc;
 }
+
+int launch_stage_vec(int kind, const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
+                     int sm_count) {
+  switch (c.cpw) {
+    case 2: return launch_stage_vec_g2(kind, c, ch, term, H, st, sm_count);
+    case 4: return launch_stage_vec_g4(kind, c, ch, term, H, st, sm_count);
+    default: return launch_stage_vec_g1(kind, c, ch, term, H, st, sm_count);
+  }
+}
+
+int launch_stage_vec_batch(int kind, int n, const VecBatchArgs &a, cudaStream_t st, int sm_count) {
+  switch (a.cpw) {
+    case 2: return launch_stage_vec_batch_g2(kind, n, a, st, sm_count);
+    case 4: return launch_stage_vec_batch_g4(kind, n, a, st, sm_count);
+    default: return launch_stage_vec_batch_g1(kind, n, a, st, sm_count);
+  }
+}
+
+// Set by heom_propagate_static around its run creation: no tuning there.
+thread_local int g_tune_suppress = 0;
 
 // 2 pi c in rad/fs per cm^-1 (c = 2.99792458e-5 cm/fs) and k_B in cm^-1/K (2019 SI, exact ratio).
 static const double kCmToRadFs = 2.0 * 3.14159265358979323846 * 2.99792458e-5;
@@ -82,6 +106,7 @@ struct heom_run {
   int64_t steps_done = 0;
   double t_fs = 0;
   int64_t launches = 0;
+  heom_schedule sched[2] = {{100, 1}, {100, 1}};  // launch schedules: [0] body, [1] FP64 head
   // timing of the dominant kernel
   bool timing = false;
   bool pending = false;              // a begin event was recorded for the current launch
@@ -417,6 +442,11 @@ static int enqueue_record(heom_run *r) {
   return HEOM_OK;
 }
 
+namespace {
+int schedule_new_run(heom_run *r);  // the autotuner (below)
+void reschedule_cached(heom_run *r);
+}  // namespace
+
 extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int precision, int64_t max_records,
                                const double *sigma0_re, const double *sigma0_im, const double *dip_w,
                                void *device_workspace, size_t workspace_bytes, void *cuda_stream, heom_run **out) {
@@ -643,6 +673,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   *out = r;
   rc = heom_set_ados(r, 0, 1, s0r.data(), s0i.data());
   if (rc == HEOM_OK) rc = enqueue_record(r);
+  if (rc == HEOM_OK) rc = schedule_new_run(r);
   if (rc != HEOM_OK) { *out = nullptr; delete r; return rc; }
   return HEOM_OK;
 }
@@ -722,65 +753,272 @@ static int join_head(heom_run *r, cudaStream_t hs) {
   return e == cudaSuccess ? HEOM_OK : cuda_fail("head stream join", e);
 }
 
-static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, double ch) {
-  StageCommon c = common_for(r, zin, y, out);
-  const double *Hi = r->cplx_h ? r->Hi.data() : nullptr;
-  int rc;
-  const bool same_y = (y.head == zin.head && y.body == zin.body);
-  const bool no_y = (y.head == nullptr && y.body == nullptr);
-  if (r->vec) {  // coherence block: column-0 kernels
-    cudaStream_t hs = r->stream;
-    if (r->precision != HEOM_FP64) {
-      c.u_begin = 0;
-      c.u_end = r->u_split;
-      hs = fork_head(r);
-      rc = launch_stage_vec(2, c, ch, r->term.data(), r->H.data(), hs, r->sm_count);
-      if (rc) return HEOM_E_CUDA;
-      ++r->launches;
-    }
-    c.u_begin = (r->precision == HEOM_FP64) ? 0 : r->u_split;
-    c.u_end = (int)r->n_ado;
-    if (c.u_end > c.u_begin) {
-      if ((rc = timed_begin(r))) return rc;
-      rc = launch_stage_vec(r->precision == HEOM_FP64 ? 0 : 1, c, ch, r->term.data(), r->H.data(), r->stream,
-                            r->sm_count);
-      if (rc) return HEOM_E_CUDA;
-      ++r->launches;
-      if ((rc = timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y))) return rc;
-    }
-    return join_head(r, hs);
-  }
-  if (r->precision == HEOM_FP64) {
-    c.u_begin = 0;
-    c.u_end = (int)r->n_ado;
-    if ((rc = timed_begin(r))) return rc;
-    rc = launch_stage(0, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
-    if (rc) return HEOM_E_CUDA;
-    ++r->launches;
-    return timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y);
-  }
-  // mixed: FP64 head (levels 0, 1, on the side stream) and FP32 body
+// The FP64 head launch (ADOs u < u_split) of a mixed-precision stage, on stream s.
+static int launch_head(heom_run *r, StageCommon c, double ch, cudaStream_t s) {
   c.u_begin = 0;
   c.u_end = r->u_split;
-  const cudaStream_t hs = fork_head(r);
-  rc = launch_stage(2, c, ch, r->term.data(), r->H.data(), Hi, hs, r->sm_count);
+  c.occ_pct = r->sched[1].occupancy_pct;
+  c.cpw = r->sched[1].chunks_per_warp;
+  const double *Hi = r->cplx_h ? r->Hi.data() : nullptr;
+  const int rc = r->vec ? launch_stage_vec(2, c, ch, r->term.data(), r->H.data(), s, r->sm_count)
+                        : launch_stage(2, c, ch, r->term.data(), r->H.data(), Hi, s, r->sm_count);
   if (rc) return HEOM_E_CUDA;
   ++r->launches;
-  c.u_begin = r->u_split;
+  return HEOM_OK;
+}
+
+// The body launch of a stage (every ADO for FP64, u >= u_split otherwise), on stream s.
+static int launch_body(heom_run *r, StageCommon c, double ch, cudaStream_t s) {
+  c.u_begin = (r->precision == HEOM_FP64) ? 0 : r->u_split;
   c.u_end = (int)r->n_ado;
-  if (c.u_end > c.u_begin) {
-    if ((rc = timed_begin(r))) return rc;
-    rc = 1;
+  if (c.u_end <= c.u_begin) return HEOM_OK;
+  c.occ_pct = r->sched[0].occupancy_pct;
+  c.cpw = r->sched[0].chunks_per_warp;
+  const double *Hi = r->cplx_h ? r->Hi.data() : nullptr;
+  const bool fp64 = r->precision == HEOM_FP64;
+  int rc = 1;
+  if (r->vec) {
+    rc = launch_stage_vec(fp64 ? 0 : 1, c, ch, r->term.data(), r->H.data(), s, r->sm_count);
+  } else if (fp64) {
+    rc = launch_stage(0, c, ch, r->term.data(), r->H.data(), Hi, s, r->sm_count);
+  } else {
     if (r->precision == HEOM_SPLIT_TF32 && r->herm && !r->cplx_h) {  // tensor-core commutator
-      rc = launch_stage_tc_a(c, ch, r->term.data(), r->H.data(), r->stream, r->sm_count);
-      if (rc == 1) rc = launch_stage_tc_b(c, ch, r->term.data(), r->H.data(), r->stream, r->sm_count);
+      rc = launch_stage_tc_a(c, ch, r->term.data(), r->H.data(), s, r->sm_count);
+      if (rc == 1) rc = launch_stage_tc_b(c, ch, r->term.data(), r->H.data(), s, r->sm_count);
     }
-    if (rc == 1) rc = launch_stage(1, c, ch, r->term.data(), r->H.data(), Hi, r->stream, r->sm_count);
-    if (rc) return HEOM_E_CUDA;
-    ++r->launches;
+    if (rc == 1) rc = launch_stage(1, c, ch, r->term.data(), r->H.data(), Hi, s, r->sm_count);
+  }
+  if (rc) return HEOM_E_CUDA;
+  ++r->launches;
+  return HEOM_OK;
+}
+
+static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, double ch) {
+  const StageCommon c = common_for(r, zin, y, out);
+  const bool same_y = (y.head == zin.head && y.body == zin.body);
+  const bool no_y = (y.head == nullptr && y.body == nullptr);
+  int rc;
+  cudaStream_t hs = r->stream;
+  if (r->precision != HEOM_FP64) {  // FP64 head (levels 0, 1) on the side stream
+    hs = fork_head(r);
+    if ((rc = launch_head(r, c, ch, hs))) return rc;
+  }
+  if ((int)r->n_ado > ((r->precision == HEOM_FP64) ? 0 : r->u_split)) {
+    if ((rc = timed_begin(r))) return rc;
+    if ((rc = launch_body(r, c, ch, r->stream))) return rc;
     if ((rc = timed_end(r, (same_y || no_y) ? r->bytes_stage_noy : r->bytes_stage_y))) return rc;
   }
   return join_head(r, hs);
+}
+
+// ------------------------------------------------------------------------------------------------
+// launch schedules and the autotuner: every candidate is timed on the run's own stage-1 launch
+// (zin = y, out = zA; y is not written) and the fastest is kept, per run and in a process-wide
+// cache.  All schedules compute the same sums in the same order, so the choice changes only time.
+
+namespace {
+std::mutex g_tune_mu;                                    // guards the cache
+std::map<std::array<int, 7>, heom_schedule> g_tune_cache;  // (layout, precision, part, n, herm, cplx, log2 ADOs)
+std::atomic<int> g_autotune{3};                          // timed launches per candidate at creation (0: off)
+heom_schedule g_default[3] = {{100, 1}, {100, 1}, {100, 1}};  // per layout, without cache entry or tuning
+
+heom_schedule default_for(int layout) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_default[layout];
+}
+
+int ilog2(int64_t x) {
+  int b = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+std::vector<heom_schedule> candidates(int layout) {
+  std::vector<heom_schedule> v;
+  if (layout == 0) {
+    for (int occ : {100, 75, 50}) v.push_back(heom_schedule{occ, 1});
+  } else {
+    for (int cpw : {1, 2, 4})
+      for (int occ : {100, 50}) v.push_back(heom_schedule{occ, cpw});
+  }
+  return v;  // the default {100, 1} first: ties keep it
+}
+
+bool valid_schedule(const heom_schedule &s) {
+  return s.occupancy_pct >= 1 && s.occupancy_pct <= 100 &&
+         (s.chunks_per_warp == 1 || s.chunks_per_warp == 2 || s.chunks_per_warp == 4);
+}
+
+std::array<int, 7> run_key(const heom_run *r, int part) {
+  const int64_t cnt = part == 1 ? r->u_split : r->n_ado - (r->precision == HEOM_FP64 ? 0 : r->u_split);
+  return {r->vec ? 1 : 0, r->precision, part, r->n, r->herm ? 1 : 0, r->cplx_h ? 1 : 0, ilog2(cnt)};
+}
+
+bool cache_get(const std::array<int, 7> &k, heom_schedule *out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune_cache.find(k);
+  if (it == g_tune_cache.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void cache_put(const std::array<int, 7> &k, const heom_schedule &s) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[k] = s;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
+// Times probe(schedule) for every candidate (one warm-up, reps timed launches each, on stream s);
+// returns the index of the fastest in *best.
+template <typename Probe>
+int time_candidates(const std::vector<heom_schedule> &cand, int reps, cudaStream_t s, Probe probe,
+                    std::vector<double> &ms, int *best) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int rc = HEOM_OK;
+  ms.assign(cand.size(), 0.0);
+  *best = 0;
+  for (size_t i = 0; i < cand.size() && e == cudaSuccess && rc == HEOM_OK; ++i) {
+    if ((rc = probe(cand[i]))) break;
+    e = cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && e == cudaSuccess && rc == HEOM_OK; ++k) rc = probe(cand[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    ms[i] = (double)t / reps;
+    if (ms[i] < ms[*best]) *best = (int)i;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc != HEOM_OK) return rc;
+  return e == cudaSuccess ? HEOM_OK : cuda_fail("autotune timing", e);
+}
+
+int tune_part(heom_run *r, int part, int reps, std::vector<heom_schedule> &tried, std::vector<double> &ms) {
+  if (capturing(r->stream)) {
+    set_error("heom_tune: the run's stream is being captured");
+    return HEOM_E_STATE;
+  }
+  tried = candidates(r->vec ? 1 : 0);
+  const heom_schedule keep = r->sched[part];
+  const StageCommon c = common_for(r, r->y, r->y, r->zA);
+  int best = 0;
+  const int rc = time_candidates(tried, reps, r->stream, [&](const heom_schedule &sc) {
+    r->sched[part] = sc;
+    return part == 1 ? launch_head(r, c, 0.25, r->stream) : launch_body(r, c, 0.25, r->stream);
+  }, ms, &best);
+  if (rc != HEOM_OK) {
+    r->sched[part] = keep;
+    return rc;
+  }
+  r->sched[part] = tried[best];
+  cache_put(run_key(r, part), tried[best]);
+  return HEOM_OK;
+}
+
+void reschedule_cached(heom_run *r) {
+  for (int part = 0; part < 2; ++part) {
+    r->sched[part] = default_for(r->vec ? 1 : 0);
+    if (part == 0 || r->precision != HEOM_FP64) cache_get(run_key(r, part), &r->sched[part]);
+  }
+}
+
+// The schedule of each part of a new run: the cache, else the tuner (if on), else the default.
+int schedule_new_run(heom_run *r) {
+  const int reps = g_autotune.load();
+  for (int part = 0; part < (r->precision == HEOM_FP64 ? 1 : 2); ++part) {
+    heom_schedule s{100, 1};
+    r->sched[part] = default_for(r->vec ? 1 : 0);
+    if (cache_get(run_key(r, part), &s)) {
+      r->sched[part] = s;
+    } else if (reps > 0 && !g_tune_suppress && !capturing(r->stream)) {
+      std::vector<heom_schedule> tried;
+      std::vector<double> ms;
+      const int rc = tune_part(r, part, reps, tried, ms);
+      if (rc != HEOM_OK) return rc;
+    }
+  }
+  return HEOM_OK;
+}
+}  // namespace
+
+extern "C" int heom_schedule_candidates(int layout, heom_schedule *out, int cap) {
+  if (layout < 0 || layout > 2 || cap < 0 || (cap > 0 && !out)) {
+    set_error("heom_schedule_candidates: layout 0..2, cap >= 0, out for cap > 0");
+    return HEOM_E_ARG;
+  }
+  const std::vector<heom_schedule> v = candidates(layout);
+  for (int i = 0; i < cap && i < (int)v.size(); ++i) out[i] = v[i];
+  return (int)v.size();
+}
+
+extern "C" int heom_tune(heom_run *r, int part, int reps, heom_schedule *tried, double *ms, int cap, int *n_tried,
+                         heom_schedule *chosen) {
+  if (!r || reps < 1 || part < 0 || part > 1 || (part == 1 && r->precision == HEOM_FP64) || cap < 0) {
+    set_error("heom_tune: need a run, reps >= 1, part 0 or 1 (1 only with an FP64 head), cap >= 0");
+    return HEOM_E_ARG;
+  }
+  std::vector<heom_schedule> t;
+  std::vector<double> m;
+  const int rc = tune_part(r, part, reps, t, m);
+  if (rc != HEOM_OK) return rc;
+  for (int i = 0; i < cap && i < (int)t.size(); ++i) {
+    if (tried) tried[i] = t[i];
+    if (ms) ms[i] = m[i];
+  }
+  if (n_tried) *n_tried = (int)t.size();
+  if (chosen) *chosen = r->sched[part];
+  return HEOM_OK;
+}
+
+extern "C" int heom_set_autotune(int reps) {
+  if (reps < 0) return g_autotune.load();
+  return g_autotune.exchange(reps);
+}
+
+extern "C" int heom_get_schedule(const heom_run *r, int part, heom_schedule *out) {
+  if (!r || !out || part < 0 || part > 1 || (part == 1 && r->precision == HEOM_FP64)) {
+    set_error("heom_get_schedule: need a run, out, part 0 or 1 (1 only with an FP64 head)");
+    return HEOM_E_ARG;
+  }
+  *out = r->sched[part];
+  return HEOM_OK;
+}
+
+extern "C" int heom_set_schedule(heom_run *r, int part, const heom_schedule *s) {
+  if (!r || !s || part < 0 || part > 1 || (part == 1 && r->precision == HEOM_FP64) || !valid_schedule(*s)) {
+    set_error("heom_set_schedule: need a run, part 0 or 1 (1 only with an FP64 head), occupancy_pct 1..100, "
+              "chunks_per_warp 1, 2 or 4");
+    return HEOM_E_ARG;
+  }
+  r->sched[part] = *s;
+  return HEOM_OK;
+}
+
+extern "C" int heom_set_default_schedule(int layout, const heom_schedule *s) {
+  if (layout < 0 || layout > 2 || (s && !valid_schedule(*s))) {
+    set_error("heom_set_default_schedule: layout 0..2 and a valid schedule (or NULL)");
+    return HEOM_E_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_default[layout] = s ? *s : heom_schedule{100, 1};
+  return HEOM_OK;
+}
+
+extern "C" int heom_tune_cache_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.clear();
+  return HEOM_OK;
 }
 
 extern "C" int heom_run_set_timing(heom_run *r, int enable) {
@@ -953,6 +1191,7 @@ static int leave_vec(heom_run *r) {
   r->bytes_stage_noy = r->bytes_full_noy;
   r->flops_gen = r->flops_full;
   r->flops_herm = r->flops_full;
+  reschedule_cached(r);  // the matrix-layout kernels: their own cache entries, else the default
   return HEOM_OK;
 }
 
@@ -1128,6 +1367,16 @@ static const int64_t kBatchGroupMaxAdos = 50000;
 // ragged batches: the stage launches of many runs, each on one of a pool of streams, captured into
 // one CUDA graph that advances every run by steps_per_launch RK4 steps per replay.
 
+// A schedule for a batched column-0 launch over runs of n states with the given ADO counts: the
+// prefix sums of the runs' warp steps (vec_group(n, cpw) chunks of floor(32 / n) ADOs each).
+static void set_batch_schedule(VecBatchArgs &x, const std::vector<int64_t> &ados, int n, const heom_schedule &sc) {
+  const int64_t sa = (int64_t)vec_group(n, sc.chunks_per_warp) * (32 / n);
+  x.chunk0[0] = 0;
+  for (size_t q = 0; q < ados.size(); ++q) x.chunk0[q + 1] = x.chunk0[q] + (ados[q] + sa - 1) / sa;
+  x.occ_pct = sc.occupancy_pct;
+  x.cpw = sc.chunks_per_warp;
+}
+
 struct heom_batch {
   std::vector<heom_run *> runs;
   std::vector<cudaStream_t> pool;
@@ -1145,6 +1394,8 @@ struct heom_batch {
   std::vector<bool> gfp64;
   std::vector<cudaStream_t> gstream;
   std::vector<std::vector<VecBatchArgs>> gargs;
+  std::vector<std::array<heom_schedule, 2>> gsched;  // per group: [0] body, [1] FP64 head
+  std::vector<std::array<std::vector<int64_t>, 2>> gados;  // per group and part: each run's ADO count
   ~heom_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1220,12 +1471,10 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
   for (const auto &gv : groups) {
     cudaStream_t gs = b->pool[gi++ % P];
     const bool fp64 = b->runs[gv[0]]->precision == HEOM_FP64;
-    const int n = b->runs[gv[0]]->n, A = 32 / n;
+    const int n = b->runs[gv[0]]->n;
     std::vector<VecBatchArgs> ba(8);
-    for (int k = 0; k < 8; ++k) {
-      ba[k].nruns = (int)gv.size();
-      ba[k].chunk0[0] = 0;
-    }
+    std::array<std::vector<int64_t>, 2> ados;
+    for (int k = 0; k < 8; ++k) ba[k].nruns = (int)gv.size();
     for (size_t q = 0; q < gv.size(); ++q) {
       heom_run *r = b->runs[gv[q]];
       std::vector<VecRunDesc> hd(8);
@@ -1243,15 +1492,15 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
           for (int a = 0; a < r->n; ++a)
             for (int c2 = 0; c2 < r->n; ++c2) d.H[a * kMaxStates + c2] = r->H[a * r->n + c2];
           for (int a = 0; a < r->n; ++a) d.term[a] = r->term[a];
-          VecBatchArgs &x = ba[st * 2 + part];
-          x.d[q] = r->desc_dev + st * 2 + part;
-          x.chunk0[q + 1] = x.chunk0[q] + (d.c.u_end - d.c.u_begin + A - 1) / A;
+          ba[st * 2 + part].d[q] = r->desc_dev + st * 2 + part;
+          if (st == 0) ados[part == 0 ? 1 : 0].push_back(std::max(0, d.c.u_end - d.c.u_begin));
         }
       cudaError_t ec = cudaMemcpy(r->desc_dev, hd.data(), 8 * sizeof(VecRunDesc), cudaMemcpyHostToDevice);
       if (ec != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: stage arguments", ec); }
       r->desc_owner = b;
     }
     b->gargs.push_back(std::move(ba));
+    b->gados.push_back(std::move(ados));
     b->gstream.push_back(gs);
     b->gfp64.push_back(fp64);
     b->gn.push_back(n);
@@ -1261,6 +1510,39 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
   for (heom_run *r : b->runs) {
     e = cudaStreamSynchronize(r->stream);
     if (e != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: run stream", e); }
+  }
+  // launch schedules of the grouped launches: the cache, else the tuner (if on; probes are stage-1
+  // launches, which write only zA), else the default
+  const int reps = g_autotune.load();
+  for (size_t g = 0; g < b->gruns.size(); ++g) {
+    std::array<heom_schedule, 2> gs{default_for(2), default_for(2)};
+    for (int part = 0; part < (b->gfp64[g] ? 1 : 2); ++part) {
+      int64_t cnt = 0;
+      for (int i : b->gruns[g]) {
+        const heom_run *r = b->runs[i];
+        cnt += part == 1 ? r->u_split : r->n_ado - (b->gfp64[g] ? 0 : r->u_split);
+      }
+      const std::array<int, 7> key{2, b->gfp64[g] ? 0 : 1, part, b->gn[g], 0, 0, ilog2(cnt)};
+      if (cache_get(key, &gs[part]) || reps <= 0) continue;
+      const int kind = part == 1 ? 2 : (b->gfp64[g] ? 0 : 1);
+      VecBatchArgs &probe = b->gargs[g][part == 1 ? 0 : 1];  // stage 1 (zin = y, out = zA) of that part
+      const std::vector<heom_schedule> cand = candidates(2);
+      std::vector<double> ms;
+      int best = 0;
+      const int rc2 = time_candidates(cand, reps, b->gstream[g], [&](const heom_schedule &sc) {
+        set_batch_schedule(probe, b->gados[g][part], b->gn[g], sc);
+        return launch_stage_vec_batch(kind, b->gn[g], probe, b->gstream[g], b->runs[0]->sm_count) ? HEOM_E_CUDA
+                                                                                                 : HEOM_OK;
+      }, ms, &best);
+      if (rc2 != HEOM_OK) { delete b; return rc2; }
+      gs[part] = cand[best];
+      cache_put(key, gs[part]);
+    }
+    for (int k = 0; k < 8; ++k) {  // argument sets st * 2 + {0: head, 1: body}
+      const int part = k % 2 == 0 ? 1 : 0;
+      set_batch_schedule(b->gargs[g][k], b->gados[g][part], b->gn[g], gs[part]);
+    }
+    b->gsched.push_back(gs);
   }
   e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { delete b; return cuda_fail("heom_batch_create: begin capture", e); }
@@ -1377,6 +1659,18 @@ extern "C" int heom_batch_launch(heom_batch *b, int64_t n_launches) {
     r->records_host += recs * n_launches;
     r->launches += n_launches * b->launches_per_replay[i];
   }
+  return HEOM_OK;
+}
+
+extern "C" int heom_batch_schedule(const heom_batch *b, int g, int part, heom_schedule *out, int *n_groups) {
+  if (!b) { set_error("heom_batch_schedule: NULL batch"); return HEOM_E_ARG; }
+  if (n_groups) *n_groups = (int)b->gsched.size();
+  if (g == -1 && !out) return HEOM_OK;
+  if (g < 0 || g >= (int)b->gsched.size() || part < 0 || part > 1 || !out) {
+    set_error("heom_batch_schedule: group out of range, part 0 or 1, out needed");
+    return HEOM_E_ARG;
+  }
+  *out = b->gsched[g][part];
   return HEOM_OK;
 }
 

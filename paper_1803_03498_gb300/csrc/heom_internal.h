@@ -63,12 +63,35 @@ struct StageCommon {
   int cplx_h;           // H has an imaginary part
   int herm;             // every ADO is Hermitian: gather row s only, and s H = (H s)^dagger
   int *err;             // device flag: a bounded device-side wait gave up (tensor-core kernel)
+  int occ_pct;          // schedule: grid sized for this percentage of the CTAs that fit on an SM
+  int cpw;              // schedule: column-0 kernels' chunks per warp step (1, 2, 4)
 };
 
-// Coherence-block (column-0) stage kernels (vec_stage.cu): kind 0 FP64, 1 mixed body (FP32),
-// 2 mixed head (FP64 compute, FP32 body neighbours).
+// Nonzero while heom_propagate_static creates its run: the autotuner stays off there.
+extern thread_local int g_tune_suppress;
+
+// Chunks of floor(32 / n) ADOs that a column-0 warp step holds for a schedule's chunks per warp g:
+// g, capped so that a step holds at most 32 ADOs (a link record names its ADO by u mod 32).
+__host__ __device__ constexpr int vec_group(int n, int g) { return g < 32 / (32 / n) ? g : 32 / (32 / n); }
+
+// CTAs per SM of a persistent grid for a schedule's occupancy percentage (at least 1).
+inline int sched_ctas(int per_sm, int occ_pct) {
+  const int b = (occ_pct <= 0 || occ_pct >= 100) ? per_sm : per_sm * occ_pct / 100;
+  return b < 1 ? 1 : b;
+}
+
+// Coherence-block (column-0) stage kernels (vec_stage_g{1,2,4}.cu, one unit per chunks-per-warp
+// value): kind 0 FP64, 1 mixed body (FP32), 2 mixed head (FP64 compute, FP32 body neighbours).
+// launch_stage_vec picks the unit from c.cpw.
 int launch_stage_vec(int kind, const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
                      int sm_count);
+#define HEOM_DECLARE_VEC(R)                                                                                 \
+  int launch_stage_vec_g##R(int kind, const StageCommon &c, double ch, const double *term, const double *H, \
+                            cudaStream_t st, int sm_count);
+HEOM_DECLARE_VEC(1)
+HEOM_DECLARE_VEC(2)
+HEOM_DECLARE_VEC(4)
+#undef HEOM_DECLARE_VEC
 
 // Stage arguments of one run for the batched column-0 kernel; lives in the run's workspace.
 struct VecRunDesc {
@@ -80,11 +103,15 @@ struct VecRunDesc {
 constexpr int kBatchMaxRuns = 1024;   // runs per batched launch (kernel-parameter space)
 struct VecBatchArgs {
   const VecRunDesc *d[kBatchMaxRuns];
-  int64_t chunk0[kBatchMaxRuns + 1];  // prefix sums of the runs' chunk counts
+  int64_t chunk0[kBatchMaxRuns + 1];  // prefix sums of the runs' warp-step counts (for cpw)
   int nruns;
+  int occ_pct, cpw;                   // schedule of the launch (the runs' own schedules do not apply)
 };
 // One launch of the batched column-0 kernel for runs of n states (kind as launch_stage_vec).
 int launch_stage_vec_batch(int kind, int n, const VecBatchArgs &a, cudaStream_t st, int sm_count);
+int launch_stage_vec_batch_g1(int kind, int n, const VecBatchArgs &a, cudaStream_t st, int sm_count);
+int launch_stage_vec_batch_g2(int kind, int n, const VecBatchArgs &a, cudaStream_t st, int sm_count);
+int launch_stage_vec_batch_g4(int kind, int n, const VecBatchArgs &a, cudaStream_t st, int sm_count);
 
 // Tensor-core (split-TF32) form of the FP32 body stage: Hermitian runs with real H and N <= 16.
 // Returns 1 when it does not cover n_states.

@@ -90,8 +90,10 @@ extern "C" int heom_propagate_static(const heom_system *sys, const heom_hier *h,
   // heom_run_create zeroes the state copies and the record counter it uses in the array, so what
   // an earlier call left there does not leak into this one.
   heom_run *r = nullptr;
+  ++g_tune_suppress;  // no autotuning here: cached schedules or the default
   rc = heom_run_create(sys, h, precision, max_records, sigma0_re, sigma0_im, dip_w, ws, kStaticBytes, cuda_stream,
                        &r);
+  --g_tune_suppress;
   if (rc != HEOM_OK) return rc;
   rc = heom_propagate(r, dt_fs, n_steps, obs_stride);
   if (rc == HEOM_OK) rc = heom_observables(r, records_out, cap_records, written);

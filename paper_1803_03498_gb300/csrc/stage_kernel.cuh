@@ -693,7 +693,7 @@ int launch_v(const StageArgs<CT> &a, cudaStream_t st, int sm_count) {
   constexpr int A = StageShape<N, CT, BT>::A;
   const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
   const int blocks_needed = (n_chunks + WARPS - 1) / WARPS;
-  const int grid = std::max(1, std::min(blocks_needed, per_sm * sm_count));
+  const int grid = std::max(1, std::min(blocks_needed, sched_ctas(per_sm, c.occ_pct) * sm_count));
   stage_kernel<N, CT, BT, CPLX><<<grid, WARPS * 32, smem, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

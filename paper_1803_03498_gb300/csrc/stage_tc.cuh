@@ -430,7 +430,7 @@ int launch_tc(const StageCommon &c, double ch, const double *term, const double 
   constexpr int A = StageShape<N, float, float>::A;
   const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
   const int blocks_needed = (n_chunks + kTcWarps - 1) / kTcWarps;
-  const int grid = std::max(1, std::min(blocks_needed, per_sm * sm_count));
+  const int grid = std::max(1, std::min(blocks_needed, sched_ctas(per_sm, c.occ_pct) * sm_count));
   stage_tc_kernel<N><<<grid, kTcWarps * 32, smem, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

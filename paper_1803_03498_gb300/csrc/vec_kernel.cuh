@@ -9,10 +9,15 @@
 //     (L x)_a = -i sum_b (H_ab - H_00 delta_ab) x_b - (sum_l n_l gamma_l + Delta_a) x_a
 //               + sum over the links of u through a mode of state a of R v_a
 // with the link coefficients R of the full form (its column part and diagonal part vanish here).
-// out_u = y_u + ch (L zin)_u as in stage_kernel (Horner RK4).  Lane (a, i) of a warp holds element i
-// of ADO u0 + a (A = floor(32 / N) ADOs per warp); H x goes through warp shuffles.  The links of a
-// chunk are taken 32 records at a time: each lane loads one record and the element of its
-// neighbour, and the products reach the owning lanes by warp shuffles.
+// out_u = y_u + ch (L zin)_u as in stage_kernel (Horner RK4).  A chunk is A = floor(32 / N)
+// consecutive ADOs; lane (a, i) of a warp holds element i of ADO a of a chunk, and H x goes through
+// warp shuffles.  A warp works on G consecutive chunks at once (G, the chunks per warp, is a
+// launch-schedule choice of the autotuner; at most 32 ADOs per warp step): each lane holds one
+// element of each, and the link records of all of them load together, G per lane per window of 32 G,
+// followed by the neighbour elements they name.  The products reach their owning lanes by warp
+// shuffles in record order.  Every G sums the same terms in the same order for each element, and
+// the serial memory round trips of a warp step (offsets, records, neighbour elements) are shared
+// by G chunks.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -52,80 +57,116 @@ __device__ __forceinline__ typename VCplx<CT>::type vec_load(const StateView &s,
   return r;
 }
 
-// One chunk (A = floor(32 / N) consecutive ADOs starting at u0 = c.u_begin + chn A) of the stage
-// out = y + ch L zin.  kOwnHead: CT = double, BT = float -- the FP64 head kernel of a mixed-precision
-// run (its own ADOs are in the head region); otherwise the own ADOs are in the body region of storage
-// type BT == CT.  hrow: row li of H; h00 = H_00; term_i = Delta of state li.
-template <int N, typename CT, typename BT>
-__device__ __forceinline__ void vec_chunk(const StageCommon &c, const CT (&hrow)[N], CT h00, CT term_i, CT ch,
-                                          int chn, int lane) {
+// One warp step: GE = vec_group(N, G) chunks, i.e. the SA = GE A consecutive ADOs starting at
+// u0 = c.u_begin + step SA, of the stage out = y + ch L zin.  kOwnHead: CT = double, BT = float -- the
+// FP64 head kernel of a mixed-precision run (its own ADOs are in the head region); otherwise the
+// own ADOs are in the body region of storage type BT == CT.  hrow: row li of H; h00 = H_00;
+// term_i = Delta of state li.
+template <int N, typename CT, typename BT, int G>
+__device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[N], CT h00, CT term_i, CT ch,
+                                         int step, int lane) {
   using C2 = typename VCplx<CT>::type;
   constexpr int A = 32 / N;
+  constexpr int GE = vec_group(N, G);
+  constexpr int SA = GE * A;
   constexpr bool kOwnHead = sizeof(CT) == 8 && sizeof(BT) == 4;
   const int la = lane / N, li = lane - la * N;
   const bool lane_ok = la < A;
   const bool has_y = (c.y.head != nullptr) || (c.y.body != nullptr);
   const LinkRec<CT> *recs = reinterpret_cast<const LinkRec<CT> *>(kOwnHead ? c.recs_head : c.recs_body);
   const int64_t rbase = kOwnHead ? 0 : c.rec_split;
-  const int u0 = c.u_begin + chn * A;
-  const int cnt = min(A, c.u_end - u0);
-  const bool active = lane_ok && la < cnt;
-  const int64_t u = u0 + la;
-  C2 x;
-  x.x = 0;
-  x.y = 0;
-  C2 yv = x;
-  if (active) {
-    x = vec_load<N, CT, BT>(c.zin, c.u_split, u, li);
-    if (has_y) yv = vec_load<N, CT, BT>(c.y, c.u_split, u, li);
-  }
-  // -i (H x)_i + i H_00 x_i
-  CT rr = -h00 * x.y, ri = h00 * x.x;
+  const int u0 = c.u_begin + step * SA;
+  const int cnt = min(SA, c.u_end - u0);
+  C2 x[GE], yv[GE];
+  CT rr[GE], ri[GE];
 #pragma unroll
-  for (int b = 0; b < N; ++b) {
-    const CT xr = __shfl_sync(0xffffffffu, x.x, min(la, A - 1) * N + b);
-    const CT xi = __shfl_sync(0xffffffffu, x.y, min(la, A - 1) * N + b);
-    rr = fma(hrow[b], xi, rr);
-    ri = fma(-hrow[b], xr, ri);
+  for (int g = 0; g < GE; ++g) {
+    const int a = g * A + la;
+    x[g].x = 0;
+    x[g].y = 0;
+    yv[g] = x[g];
+    if (lane_ok && a < cnt) {
+      x[g] = vec_load<N, CT, BT>(c.zin, c.u_split, u0 + a, li);
+      if (has_y) yv[g] = vec_load<N, CT, BT>(c.y, c.u_split, u0 + a, li);
+    }
   }
-  if (active) {
-    const CT f = (CT)c.gsum[u] + term_i;
-    rr = fma(-f, x.x, rr);
-    ri = fma(-f, x.y, ri);
+  // -i (H x)_i + i H_00 x_i, then decay and terminator
+#pragma unroll
+  for (int g = 0; g < GE; ++g) {
+    rr[g] = -h00 * x[g].y;
+    ri[g] = h00 * x[g].x;
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      const CT xr = __shfl_sync(0xffffffffu, x[g].x, min(la, A - 1) * N + b);
+      const CT xi = __shfl_sync(0xffffffffu, x[g].y, min(la, A - 1) * N + b);
+      rr[g] = fma(hrow[b], xi, rr[g]);
+      ri[g] = fma(-hrow[b], xr, ri[g]);
+    }
+    const int a = g * A + la;
+    if (lane_ok && a < cnt) {
+      const CT f = (CT)c.gsum[u0 + a] + term_i;
+      rr[g] = fma(-f, x[g].x, rr[g]);
+      ri[g] = fma(-f, x[g].y, ri[g]);
+    }
   }
-  // links, 32 records of the chunk at a time: the lane holding a record loads its neighbour's
-  // element s and forms R v_s; the contributions then go to their owner lanes (a, s), a = the
-  // record's ADO in the chunk (tag u mod 32), by a uniform shuffle loop
+  // links, 32 GE records of the step at a time: lane l loads records base + 32 q + l (q < GE), then
+  // the neighbour element s each names, and forms R v_s; the contributions then go to their owner
+  // (chunk g, lane (a, s)), o = g A + a the record's ADO in the step (tag u mod 32), by a uniform
+  // shuffle loop over the records in order
   {
     const int64_t lo = c.link_off[u0], hi = c.link_off[u0 + cnt];
-    for (int64_t base = lo; base < hi; base += 32) {
-      const int64_t t = base + lane;
-      int owner = -1;
-      CT cr = 0, ci = 0;
-      if (t < hi) {
-        const LinkRec<CT> r = recs[t - rbase];
-        const int st = r.s & kRecStateMask;
-        owner = (((r.s >> 8) - u0) & 31) * N + st;
-        const C2 v = vec_load<N, CT, BT>(c.zin, c.u_split, r.v, st);
-        cr = fma(r.re, v.x, -r.im * v.y);
-        ci = fma(r.re, v.y, r.im * v.x);
+    for (int64_t base = lo; base < hi; base += 32 * GE) {
+      LinkRec<CT> rq[GE];
+#pragma unroll
+      for (int q = 0; q < GE; ++q) {
+        const int64_t t = base + q * 32 + lane;
+        if (t < hi) rq[q] = recs[t - rbase];
       }
-      const int w = (int)min((int64_t)32, hi - base);
-      for (int k = 0; k < w; ++k) {
-        const int o = __shfl_sync(0xffffffffu, owner, k);
-        const CT pr = __shfl_sync(0xffffffffu, cr, k);
-        const CT pi = __shfl_sync(0xffffffffu, ci, k);
-        if (o == lane) {
-          rr += pr;
-          ri += pi;
+      int owner[GE];
+      CT cr[GE], ci[GE];
+#pragma unroll
+      for (int q = 0; q < GE; ++q) {
+        const int64_t t = base + q * 32 + lane;
+        owner[q] = -1;
+        cr[q] = 0;
+        ci[q] = 0;
+        if (t < hi) {
+          const int st = rq[q].s & kRecStateMask;
+          const int o = ((rq[q].s >> 8) - u0) & 31;
+          const int og = o / A;
+          owner[q] = og * 32 + (o - og * A) * N + st;
+          const C2 v = vec_load<N, CT, BT>(c.zin, c.u_split, rq[q].v, st);
+          cr[q] = fma(rq[q].re, v.x, -rq[q].im * v.y);
+          ci[q] = fma(rq[q].re, v.y, rq[q].im * v.x);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < GE; ++q) {
+        const int64_t b0 = base + q * 32;
+        if (b0 >= hi) break;  // uniform across the warp
+        const int w = (int)min((int64_t)32, hi - b0);
+        for (int k = 0; k < w; ++k) {
+          const int o = __shfl_sync(0xffffffffu, owner[q], k);
+          const CT pr = __shfl_sync(0xffffffffu, cr[q], k);
+          const CT pi = __shfl_sync(0xffffffffu, ci[q], k);
+#pragma unroll
+          for (int g = 0; g < GE; ++g)
+            if (o == g * 32 + lane) {
+              rr[g] += pr;
+              ri[g] += pi;
+            }
         }
       }
     }
   }
-  if (active) {
+#pragma unroll
+  for (int g = 0; g < GE; ++g) {
+    const int a = g * A + la;
+    if (!(lane_ok && a < cnt)) continue;
+    const int64_t u = u0 + a;
     C2 o;
-    o.x = has_y ? fma(ch, rr, yv.x) : ch * rr;
-    o.y = has_y ? fma(ch, ri, yv.y) : ch * ri;
+    o.x = has_y ? fma(ch, rr[g], yv[g].x) : ch * rr[g];
+    o.y = has_y ? fma(ch, ri[g], yv[g].y) : ch * ri[g];
     if (kOwnHead || u < c.u_split) {
       c.out.head[u * N + li] = make_double2((double)o.x, (double)o.y);
     } else {
@@ -137,9 +178,10 @@ __device__ __forceinline__ void vec_chunk(const StageCommon &c, const CT (&hrow)
   }
 }
 
-template <int N, typename CT, typename BT>
+template <int N, typename CT, typename BT, int G>
 __global__ void __launch_bounds__(kVecWarps * 32) vec_stage_kernel(const __grid_constant__ StageArgs<CT> a) {
   constexpr int A = 32 / N;
+  constexpr int SA = vec_group(N, G) * A;
   const StageCommon &c = a.c;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kVecWarps + (threadIdx.x >> 5);
@@ -151,13 +193,14 @@ __global__ void __launch_bounds__(kVecWarps * 32) vec_stage_kernel(const __grid_
   for (int b = 0; b < N; ++b) hrow[b] = lane_ok ? a.H[li * kMaxStates + b] : (CT)0;
   const CT h00 = a.H[0];
   const CT term_i = lane_ok ? a.term[li] : (CT)0;
-  const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
-  for (int chn = gw; chn < n_chunks; chn += nw) vec_chunk<N, CT, BT>(c, hrow, h00, term_i, a.ch, chn, lane);
+  const int n_steps = (c.u_end - c.u_begin + SA - 1) / SA;
+  for (int sp = gw; sp < n_steps; sp += nw) vec_step<N, CT, BT, G>(c, hrow, h00, term_i, a.ch, sp, lane);
 }
 
-// Many runs of the same N in one launch (ragged batches): run k's chunks are the launch's chunks
-// [chunk0[k], chunk0[k+1]); its stage arguments sit in its own workspace (d[k]).
-template <int N, typename CT, typename BT>
+// Many runs of the same N in one launch (ragged batches): run k's warp steps (of vec_group(N, G)
+// chunks each) are the launch's steps [chunk0[k], chunk0[k+1]); its stage arguments sit in its own
+// workspace (d[k]).
+template <int N, typename CT, typename BT, int G>
 __global__ void __launch_bounds__(kVecWarps * 32) vec_batch_kernel(const __grid_constant__ VecBatchArgs a) {
   constexpr int A = 32 / N;
   const int lane = threadIdx.x & 31;
@@ -181,12 +224,12 @@ __global__ void __launch_bounds__(kVecWarps * 32) vec_batch_kernel(const __grid_
 #pragma unroll
     for (int b = 0; b < N; ++b) hrow[b] = lane_ok ? (CT)__ldg(&d->H[li * kMaxStates + b]) : (CT)0;
     const CT h00 = (CT)__ldg(&d->H[0]), term_i = lane_ok ? (CT)__ldg(&d->term[li]) : (CT)0;
-    vec_chunk<N, CT, BT>(c, hrow, h00, term_i, (CT)__ldg(&d->ch), (int)(g - a.chunk0[k]), lane);
+    vec_step<N, CT, BT, G>(c, hrow, h00, term_i, (CT)__ldg(&d->ch), (int)(g - a.chunk0[k]), lane);
   }
   (void)k;
 }
 
-template <int N, typename CT, typename BT>
+template <int N, typename CT, typename BT, int G>
 int launch_vec_n(const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
                  int sm_count) {
   StageArgs<CT> a;
@@ -202,17 +245,17 @@ int launch_vec_n(const StageCommon &c, double ch, const double *term, const doub
   static int per_sm = 0;
   if (per_sm == 0) {
     int ps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, vec_stage_kernel<N, CT, BT>, kVecWarps * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, vec_stage_kernel<N, CT, BT, G>, kVecWarps * 32, 0);
     if (e != cudaSuccess || ps < 1) {
       set_error(std::string("vector stage kernel: occupancy query failed: ") + cudaGetErrorString(e));
       return -4;
     }
     per_sm = ps;
   }
-  constexpr int A = 32 / N;
-  const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
-  const int grid = std::max(1, std::min((n_chunks + kVecWarps - 1) / kVecWarps, per_sm * sm_count));
-  vec_stage_kernel<N, CT, BT><<<grid, kVecWarps * 32, 0, st>>>(a);
+  constexpr int SA = vec_group(N, G) * (32 / N);
+  const int n_steps = (c.u_end - c.u_begin + SA - 1) / SA;
+  const int grid = std::max(1, std::min((n_steps + kVecWarps - 1) / kVecWarps, sched_ctas(per_sm, c.occ_pct) * sm_count));
+  vec_stage_kernel<N, CT, BT, G><<<grid, kVecWarps * 32, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("vector stage kernel launch: ") + cudaGetErrorString(e));
@@ -221,12 +264,12 @@ int launch_vec_n(const StageCommon &c, double ch, const double *term, const doub
   return 0;
 }
 
-template <int N, typename CT, typename BT>
+template <int N, typename CT, typename BT, int G>
 int launch_vec_batch_n(const VecBatchArgs &a, cudaStream_t st, int sm_count) {
   static int per_sm = 0;
   if (per_sm == 0) {
     int ps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, vec_batch_kernel<N, CT, BT>, kVecWarps * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, vec_batch_kernel<N, CT, BT, G>, kVecWarps * 32, 0);
     if (e != cudaSuccess || ps < 1) {
       set_error(std::string("batched vector kernel: occupancy query failed: ") + cudaGetErrorString(e));
       return -4;
@@ -235,14 +278,44 @@ int launch_vec_batch_n(const VecBatchArgs &a, cudaStream_t st, int sm_count) {
   }
   const int64_t total = a.chunk0[a.nruns];
   if (total <= 0) return 0;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + kVecWarps - 1) / kVecWarps, (int64_t)per_sm * sm_count));
-  vec_batch_kernel<N, CT, BT><<<grid, kVecWarps * 32, 0, st>>>(a);
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((total + kVecWarps - 1) / kVecWarps, (int64_t)sched_ctas(per_sm, a.occ_pct) * sm_count));
+  vec_batch_kernel<N, CT, BT, G><<<grid, kVecWarps * 32, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("batched vector kernel launch: ") + cudaGetErrorString(e));
     return -4;
   }
   return 0;
+}
+
+// The launchers of one chunks-per-warp value for n_states 2..kMaxStates: kind 0 FP64 (double,
+// double), 1 mixed body (float, float), 2 mixed head (double, float).
+template <int G, int N = 2>
+int vec_dispatch(int kind, const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
+                 int sm_count) {
+  if constexpr (N > kMaxStates) {
+    set_error("vector stage kernel: n_states not compiled");
+    return -1;
+  } else {
+    if (c.n != N) return vec_dispatch<G, N + 1>(kind, c, ch, term, H, st, sm_count);
+    return kind == 0 ? launch_vec_n<N, double, double, G>(c, ch, term, H, st, sm_count)
+         : kind == 1 ? launch_vec_n<N, float, float, G>(c, ch, term, H, st, sm_count)
+                     : launch_vec_n<N, double, float, G>(c, ch, term, H, st, sm_count);
+  }
+}
+
+template <int G, int N = 2>
+int vec_batch_dispatch(int kind, int n, const VecBatchArgs &a, cudaStream_t st, int sm_count) {
+  if constexpr (N > kMaxStates) {
+    set_error("batched vector kernel: n_states not compiled");
+    return -1;
+  } else {
+    if (n != N) return vec_batch_dispatch<G, N + 1>(kind, n, a, st, sm_count);
+    return kind == 0 ? launch_vec_batch_n<N, double, double, G>(a, st, sm_count)
+         : kind == 1 ? launch_vec_batch_n<N, float, float, G>(a, st, sm_count)
+                     : launch_vec_batch_n<N, double, float, G>(a, st, sm_count);
+  }
 }
 
 }  // namespace heom

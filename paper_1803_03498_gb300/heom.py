@@ -26,6 +26,8 @@ ABI_SYMBOLS = [
     "heom_observables", "heom_get_sigma0", "heom_get_ados", "heom_set_ados", "heom_rhs_eval", "heom_run_info",
     "heom_run_launches", "heom_run_set_timing", "heom_run_kernel_time", "heom_propagate_static",
     "heom_batch_create", "heom_batch_launch", "heom_batch_destroy", "heom_bath_modes", "heom_run_layout",
+    "heom_schedule_candidates", "heom_tune", "heom_set_autotune", "heom_get_schedule", "heom_set_schedule",
+    "heom_tune_cache_clear", "heom_batch_schedule", "heom_set_default_schedule",
 ]
 MATSUBARA, PADE = 0, 1
 DECOMPOSITIONS = {"matsubara": MATSUBARA, "pade": PADE}
@@ -52,6 +54,14 @@ class _System(ctypes.Structure):
         ("rescale", ctypes.c_int),
         ("decomposition", ctypes.c_int),
     ]
+
+
+class _Schedule(ctypes.Structure):
+    _fields_ = [("occupancy_pct", ctypes.c_int), ("chunks_per_warp", ctypes.c_int)]
+
+
+def _sched_tuple(s):
+    return (int(s.occupancy_pct), int(s.chunks_per_warp))
 
 
 _lib = None
@@ -93,6 +103,15 @@ def load():
     L.heom_batch_destroy.argtypes = [vp]
     L.heom_propagate_static.argtypes = [P(_System), vp, i, P(d), P(d), P(d), d, i64, i64, vp, P(d), i64, P(i64),
                                         P(d), P(d)]
+    S = _Schedule
+    L.heom_schedule_candidates.argtypes = [i, P(S), i]
+    L.heom_tune.argtypes = [vp, i, i, P(S), P(d), i, P(i), P(S)]
+    L.heom_set_autotune.argtypes = [i]
+    L.heom_get_schedule.argtypes = [vp, i, P(S)]
+    L.heom_set_schedule.argtypes = [vp, i, P(S)]
+    L.heom_tune_cache_clear.argtypes = []
+    L.heom_set_default_schedule.argtypes = [i, P(S)]
+    L.heom_batch_schedule.argtypes = [vp, i, i, P(S), P(i)]
     for name in ABI_SYMBOLS:
         if name not in ("heom_last_error", "heom_run_launches"):
             getattr(L, name).restype = ctypes.c_int
@@ -164,6 +183,35 @@ class _SysArgs:
         s.rescale = int(bool(rescale))
         s.decomposition = DECOMPOSITIONS[getattr(system, "decomposition", "matsubara")]
         self.s = s
+
+
+def schedule_candidates(layout: int):
+    """heom_schedule_candidates (host only): the (occupancy_pct, chunks_per_warp) pairs the tuner
+    times for layout 0 (matrix), 1 (column-0 run) or 2 (column-0 batch group)."""
+    L = load()
+    n = L.heom_schedule_candidates(int(layout), None, 0)
+    if n < 0:
+        _check(n)
+    buf = (_Schedule * n)()
+    L.heom_schedule_candidates(int(layout), buf, n)
+    return [_sched_tuple(x) for x in buf]
+
+
+def set_autotune(reps: int) -> int:
+    """heom_set_autotune: timed launches per candidate when runs and batches are created (0: off);
+    returns the previous value (a negative argument only queries)."""
+    return int(load().heom_set_autotune(int(reps)))
+
+
+def tune_cache_clear():
+    _check(load().heom_tune_cache_clear())
+
+
+def set_default_schedule(layout: int, schedule=None):
+    """heom_set_default_schedule: the schedule (occupancy_pct, chunks_per_warp) that parts of a layout
+    take without a cache entry or tuning; None restores (100, 1)."""
+    s = None if schedule is None else ctypes.byref(_Schedule(int(schedule[0]), int(schedule[1])))
+    _check(load().heom_set_default_schedule(int(layout), s))
 
 
 def bath_modes(system, terminator=True):
@@ -267,6 +315,26 @@ class Run:
     def launches(self) -> int:
         return int(load().heom_run_launches(self._r))
 
+    def tune(self, part: int = 0, reps: int = 3):
+        """heom_tune: time every candidate schedule of a part (0 body, 1 FP64 head); returns
+        (chosen, [(schedule, ms per launch), ...])."""
+        cap = 16
+        tried = (_Schedule * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        ch = _Schedule()
+        _check(load().heom_tune(self._r, int(part), int(reps), tried, ms, cap, ctypes.byref(n), ctypes.byref(ch)))
+        return _sched_tuple(ch), [(_sched_tuple(tried[k]), float(ms[k])) for k in range(min(n.value, cap))]
+
+    def schedule(self, part: int = 0):
+        s = _Schedule()
+        _check(load().heom_get_schedule(self._r, int(part), ctypes.byref(s)))
+        return _sched_tuple(s)
+
+    def set_schedule(self, occupancy_pct: int, chunks_per_warp: int = 1, part: int = 0):
+        s = _Schedule(int(occupancy_pct), int(chunks_per_warp))
+        _check(load().heom_set_schedule(self._r, int(part), ctypes.byref(s)))
+
     def set_timing(self, enable: bool):
         _check(load().heom_run_set_timing(self._r, int(bool(enable))))
 
@@ -298,6 +366,21 @@ class Batch:
 
     def launch(self, n_launches: int = 1):
         _check(load().heom_batch_launch(self._b, int(n_launches)))
+
+    def schedules(self):
+        """heom_batch_schedule: per group of batched column-0 launches, (body, FP64 head) schedules."""
+        L = load()
+        ng = ctypes.c_int()
+        _check(L.heom_batch_schedule(self._b, -1, 0, None, ctypes.byref(ng)))
+        out = []
+        for g in range(ng.value):
+            pair = []
+            for part in (0, 1):
+                s = _Schedule()
+                _check(L.heom_batch_schedule(self._b, g, part, ctypes.byref(s), None))
+                pair.append(_sched_tuple(s))
+            out.append(tuple(pair))
+        return out
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:

@@ -97,3 +97,24 @@ def test_run_bytes_and_argument_errors(lib):
     with pytest.raises(heom.HeomError):
         heom.run_bytes(bad, heom.Hierarchy(1, 1), "fp64", 1)
     assert "n_states" in lib.heom_last_error().decode()
+
+
+def test_schedule_candidates_and_autotune_switch(lib):
+    """The tuner's candidate sets (host only) and the process-wide switch."""
+    assert heom.schedule_candidates(0) == [(100, 1), (75, 1), (50, 1)]
+    both = [(100, 1), (50, 1), (100, 2), (50, 2), (100, 4), (50, 4)]
+    assert heom.schedule_candidates(1) == both and heom.schedule_candidates(2) == both
+    with pytest.raises(heom.HeomError) as ei:
+        heom.schedule_candidates(3)
+    assert ei.value.code == heom.HEOM_E_ARG
+    prev = heom.set_autotune(-1)  # query
+    assert prev >= 0
+    assert heom.set_autotune(5) == prev
+    assert heom.set_autotune(-1) == 5
+    heom.set_autotune(prev)
+    heom.tune_cache_clear()
+    heom.set_default_schedule(1, (50, 4))
+    heom.set_default_schedule(1, None)
+    with pytest.raises(heom.HeomError) as ei:
+        heom.set_default_schedule(0, (100, 3))
+    assert ei.value.code == heom.HEOM_E_ARG
