@@ -21,7 +21,17 @@
  *     written with the Kronecker deltas of their element-wise definitions, and the ADO rescaling
  *     (section "HEOM formalism", last two substitutions).
  *   - integrator: classic four-stage Runge-Kutta with four ADO copies (section "HEOM memory and
- *     compute requirements" and "Distributed memory HEOM implementation").
+ *     compute requirements" and "Distributed memory HEOM implementation"); a time-dependent
+ *     Hamiltonian is evaluated at each stage's time t, t + h/2, t + h/2, t + h.
+ *   - laser field in the rotating-wave approximation (section "Optical spectra", Eq. h-field-rwa
+ *     with Eq. probe_pulse): H(t) = H - g(t) M+ - conj(g(t)) M-, M- = (M+)^T, with the envelope
+ *     g(t) = E0 exp(-(t - t_c)^2 / (2 sigma^2)) exp(-i (Delta t + phi)) seen from the frame that
+ *     rotates at the reference frequency subtracted from every excitation (Delta = carrier minus
+ *     reference, phi the pulse phase); M+ = e . mu^+ is the polarisation-weighted dipole operator.
+ *   - two-exciton space (section "Dipole operators and rotational averaging"): the bath of site b
+ *     couples through its site-number operator, a diagonal V_b with 1 at every state that has site
+ *     b excited (orc_set_bath_mask); V^x, V^x V^x and V^o keep their element-wise definitions for
+ *     any diagonal V.
  *   - observables: rho = sigma_0; site populations; trace; the linear-absorption dipole
  *     correlation sum_a w_a sigma_0[a][0] (Eq. lin_abs_mukamel with mu^+ |0><0| as start).
  *
@@ -30,7 +40,8 @@
  * k_B = 0.6950348004 cm^-1/K (exact from the 2019 SI constants).  The paper is silent on units.
  *
  * Readings of the paper (each also listed in the project's design notes):
- *   - one bath per coupled state (S(b) = 1): V_b = |s_b><s_b|; several baths may share a state.
+ *   - one bath per coupled state (S(b) = 1): V_b = |s_b><s_b|; several baths may share a state;
+ *     in the two-exciton space V_b is the number operator of site b (a 0/1 diagonal).
  *   - K here is the number of Matsubara terms beyond the Drude term, so each bath has K+1 modes.
  *   - hbar = 1 throughout (the paper's hbar placement is not consistent).
  *   - the rescaling uses |c(b,k)| of the real c of the paper; when |c| < 1e-300 the mode is left
@@ -59,7 +70,12 @@ typedef struct {
 
 typedef struct {
   int N;              /* n_states */
-  cplx *H;            /* [N][N] rad/fs */
+  cplx *H;            /* [N][N] rad/fs, at the current time (orc_set_time) */
+  cplx *H0;           /* [N][N] rad/fs, without the field */
+  double *vmask;      /* [B][N]: the diagonal of V_b (0 or 1) */
+  int has_field;      /* laser field (orc_set_field) */
+  double *mup;        /* [N][N] M+ (real) */
+  double famp, ftc, fsig, fphase, fdet; /* rad/fs, fs, fs, rad, rad/fs */
   int B, K;           /* baths, Matsubara terms beyond Drude (modes per bath = K+1) */
   int *bath_state;    /* [B] */
   double *lambda, *nu, *beta; /* [B] rad/fs, 1/fs, fs */
@@ -236,6 +252,9 @@ int orc_hier_export(int M, int D, int64_t cap, uint8_t *tuples, int32_t *plus, i
 void orc_destroy(orc_model *m) {
   if (!m) return;
   free(m->H);
+  free(m->H0);
+  free(m->vmask);
+  free(m->mup);
   free(m->bath_state);
   free(m->lambda);
   free(m->nu);
@@ -338,8 +357,12 @@ orc_model *orc_create(int N, const double *H_re, const double *H_im, int B, cons
   m->terminator = terminator;
   m->rescale = rescale;
   m->H = (cplx *)malloc(sizeof(cplx) * N * N);
-  for (int i = 0; i < N * N; ++i)
-    m->H[i] = ORC_TWO_PI_C * (H_re[i] + I * (H_im ? H_im[i] : 0.0));
+  m->H0 = (cplx *)malloc(sizeof(cplx) * N * N);
+  for (int i = 0; i < N * N; ++i) {
+    m->H0[i] = ORC_TWO_PI_C * (H_re[i] + I * (H_im ? H_im[i] : 0.0));
+    m->H[i] = m->H0[i];
+  }
+  m->vmask = (double *)calloc((size_t)B * N, sizeof(double));
   m->bath_state = (int *)malloc(sizeof(int) * B);
   m->lambda = (double *)malloc(sizeof(double) * B);
   m->nu = (double *)malloc(sizeof(double) * B);
@@ -352,6 +375,7 @@ orc_model *orc_create(int N, const double *H_re, const double *H_im, int B, cons
   for (int b = 0; b < B; ++b) {
     if (bath_state[b] < 0 || bath_state[b] >= N) { orc_destroy(m); return NULL; }
     m->bath_state[b] = bath_state[b];
+    m->vmask[(size_t)b * N + bath_state[b]] = 1.0;  /* V_b = |s_b><s_b| */
     m->lambda[b] = ORC_TWO_PI_C * lambda_cm[b];
     m->nu[b] = 1.0 / tau_fs[b];
     m->beta[b] = 1.0 / (ORC_TWO_PI_C * ORC_KB_CM * T_K[b]);
@@ -395,6 +419,50 @@ orc_model *orc_create(int N, const double *H_re, const double *H_im, int B, cons
   return m;
 }
 
+/* V_b as a 0/1 diagonal over the states (mask [B][N]), replacing |s_b><s_b|: the number operator
+ * of site b in the two-exciton space.  Returns -1 on a value other than 0 or 1. */
+int orc_set_bath_mask(orc_model *m, const uint8_t *mask) {
+  for (int64_t e = 0; e < (int64_t)m->B * m->N; ++e)
+    if (mask[e] > 1) return -1;
+  for (int64_t e = 0; e < (int64_t)m->B * m->N; ++e) m->vmask[e] = (double)mask[e];
+  return 0;
+}
+
+/* H(t) = H0 - g(t) M+ - conj(g(t)) (M+)^T with g(t) = E0 exp(-(t - t_c)^2 / (2 sigma^2))
+ * exp(-i (Delta t + phi)); E0 and Delta in cm^-1.  mu_plus == NULL removes the field. */
+int orc_set_field(orc_model *m, const double *mu_plus, double amp_cm, double t_center_fs, double sigma_fs,
+                  double phase, double detuning_cm) {
+  if (!mu_plus) {
+    m->has_field = 0;
+    return 0;
+  }
+  if (!(sigma_fs > 0)) return -1;
+  const int N = m->N;
+  if (!m->mup) m->mup = (double *)malloc(sizeof(double) * N * N);
+  memcpy(m->mup, mu_plus, sizeof(double) * N * N);
+  m->famp = ORC_TWO_PI_C * amp_cm;
+  m->ftc = t_center_fs;
+  m->fsig = sigma_fs;
+  m->fphase = phase;
+  m->fdet = ORC_TWO_PI_C * detuning_cm;
+  m->has_field = 1;
+  return 0;
+}
+
+/* The Hamiltonian that orc_rhs uses from now on: H(t). */
+void orc_set_time(orc_model *m, double t_fs) {
+  const int N = m->N;
+  if (!m->has_field) {
+    for (int e = 0; e < N * N; ++e) m->H[e] = m->H0[e];
+    return;
+  }
+  const double x = (t_fs - m->ftc) / m->fsig;
+  const cplx g = m->famp * exp(-0.5 * x * x) * cexp(-I * (m->fdet * t_fs + m->fphase));
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j)
+      m->H[i * N + j] = m->H0[i * N + j] - g * m->mup[i * N + j] - conj(g) * m->mup[j * N + i];
+}
+
 int64_t orc_n_ado(const orc_model *m) { return m->h.n; }
 int orc_n_modes(const orc_model *m) { return m->M; }
 
@@ -419,13 +487,12 @@ void orc_export_hierarchy(const orc_model *m, uint8_t *tuples, int32_t *plus, in
 /* ------------------------------------------------------------------------------------------ */
 /* Superoperators, element-wise from their delta definitions.                                  */
 
-static inline double kd(int a, int b) { return a == b ? 1.0 : 0.0; }
-/* (V_s^x A)_ij = (delta_is - delta_sj) A_ij */
-static inline double vx(int s, int i, int j) { return kd(i, s) - kd(s, j); }
-/* (V_s^x V_s^x A)_ij = (1 - delta_ij)(delta_is + delta_sj) A_ij */
-static inline double vxvx(int s, int i, int j) { return (1.0 - kd(i, j)) * (kd(i, s) + kd(s, j)); }
-/* (V_s^o A)_ij = (delta_is + delta_sj) A_ij */
-static inline double vo(int s, int i, int j) { return kd(i, s) + kd(s, j); }
+/* For a diagonal V with diagonal v[]: (V^x A)_ij = (v_i - v_j) A_ij, (V^x V^x A)_ij = (v_i - v_j)^2 A_ij,
+ * (V^o A)_ij = (v_i + v_j) A_ij.  For V = |s><s| these are (delta_is - delta_sj), (1 - delta_ij)
+ * (delta_is + delta_sj) and (delta_is + delta_sj). */
+static inline double vx(const double *v, int i, int j) { return v[i] - v[j]; }
+static inline double vxvx(const double *v, int i, int j) { return (v[i] - v[j]) * (v[i] - v[j]); }
+static inline double vo(const double *v, int i, int j) { return v[i] + v[j]; }
 
 /* scale factors of the ADO rescaling */
 static double up_factor(const orc_model *m, int l, int n_l) {
@@ -461,25 +528,26 @@ static void rhs_one(const orc_model *m, int64_t u, const double *in_re, const do
   /* - sum_b [2 lambda/(beta nu) - sum_k c/gamma] V^x V^x sigma_u */
   if (m->terminator)
     for (int b = 0; b < m->B; ++b) {
-      int s = m->bath_state[b];
+      const double *v = m->vmask + (size_t)b * N;
       for (int i = 0; i < N; ++i)
-        for (int j = 0; j < N; ++j) out[i * N + j] -= m->delta_b[b] * vxvx(s, i, j) * SIG(u, i, j);
+        for (int j = 0; j < N; ++j) out[i * N + j] -= m->delta_b[b] * vxvx(v, i, j) * SIG(u, i, j);
     }
   /* + sum i V^x sigma^+  and  + sum n theta sigma^-, with the rescaled factors */
   for (int l = 0; l < M; ++l) {
-    int b = l / K1, k = l % K1, s = m->bath_state[b];
+    int b = l / K1, k = l % K1;
+    const double *v = m->vmask + (size_t)b * N;
     int32_t vp = m->h.plus[u * M + l], vm = m->h.minus[u * M + l];
     if (vp >= 0) {
       double f = up_factor(m, l, n[l]);
       for (int i = 0; i < N; ++i)
-        for (int j = 0; j < N; ++j) out[i * N + j] += I * f * vx(s, i, j) * SIG(vp, i, j);
+        for (int j = 0; j < N; ++j) out[i * N + j] += I * f * vx(v, i, j) * SIG(vp, i, j);
     }
     if (vm >= 0) {
       double f = down_factor(m, l, n[l]);
       for (int i = 0; i < N; ++i)
         for (int j = 0; j < N; ++j) {
           /* theta = i c V^x + delta_{k0} lambda nu V^o */
-          cplx theta = I * m->c[l] * vx(s, i, j) + (k == 0 ? m->lamnu[l] : 0.0) * vo(s, i, j);
+          cplx theta = I * m->c[l] * vx(v, i, j) + (k == 0 ? m->lamnu[l] : 0.0) * vo(v, i, j);
           out[i * N + j] += f * theta * SIG(vm, i, j);
         }
     }
@@ -541,13 +609,13 @@ static void record(const orc_model *m, const double *y_re, const double *y_im, c
   rec[N + 3] = ci;
 }
 
-/* Classic RK4 with four ADO copies: k1 = f(y), k2 = f(y + h/2 k1), k3 = f(y + h/2 k2),
- * k4 = f(y + h k3), y <- y + h/6 (k1 + 2 k2 + 2 k3 + k4).
+/* Classic RK4 with four ADO copies from time t0: k1 = f(t, y), k2 = f(t + h/2, y + h/2 k1),
+ * k3 = f(t + h/2, y + h/2 k2), k4 = f(t + h, y + h k3), y <- y + h/6 (k1 + 2 k2 + 2 k3 + k4).
  * y: [n][N][N] split re/im, updated in place.  Records every obs_stride steps (after the step),
  * plus one record of the start state; obs must hold (n_steps/obs_stride + 1) records.
- * w: [N] weights of the dipole correlation (may be NULL). */
-int orc_rk4(const orc_model *m, double *y_re, double *y_im, double dt_fs, int64_t n_steps,
-            int64_t obs_stride, const double *w, double *obs) {
+ * w: [N] weights of the dipole correlation (may be NULL).  Leaves H at t0 + n_steps h. */
+int orc_rk4_t(orc_model *m, double *y_re, double *y_im, double t0_fs, double dt_fs, int64_t n_steps,
+              int64_t obs_stride, const double *w, double *obs) {
   const int64_t tot = m->h.n * (int64_t)m->N * m->N;
   double *k_re = (double *)malloc(sizeof(double) * tot), *k_im = (double *)malloc(sizeof(double) * tot);
   double *x_re = (double *)malloc(sizeof(double) * tot), *x_im = (double *)malloc(sizeof(double) * tot);
@@ -559,6 +627,7 @@ int orc_rk4(const orc_model *m, double *y_re, double *y_im, double dt_fs, int64_
   const double h = dt_fs;
   const double wacc[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const double anext[3] = {0.5, 0.5, 1.0};
+  const double cstage[4] = {0.0, 0.5, 0.5, 1.0};
   int64_t rec_i = 0;
   const int rl = orc_record_len(m);
   if (obs) record(m, y_re, y_im, w, obs + (rec_i++) * rl);
@@ -567,6 +636,7 @@ int orc_rk4(const orc_model *m, double *y_re, double *y_im, double dt_fs, int64_
     memcpy(a_im, y_im, sizeof(double) * tot);
     const double *xin_re = y_re, *xin_im = y_im;
     for (int s = 0; s < 4; ++s) {
+      orc_set_time(m, t0_fs + ((double)step + cstage[s]) * h);
       orc_rhs(m, xin_re, xin_im, k_re, k_im);
       for (int64_t e = 0; e < tot; ++e) {
         a_re[e] += wacc[s] * h * k_re[e];
@@ -586,5 +656,11 @@ int orc_rk4(const orc_model *m, double *y_re, double *y_im, double dt_fs, int64_
     if (obs && obs_stride > 0 && (step + 1) % obs_stride == 0) record(m, y_re, y_im, w, obs + (rec_i++) * rl);
   }
   free(k_re); free(k_im); free(x_re); free(x_im); free(a_re); free(a_im);
+  orc_set_time(m, t0_fs + (double)n_steps * h);
   return 0;
+}
+
+int orc_rk4(orc_model *m, double *y_re, double *y_im, double dt_fs, int64_t n_steps, int64_t obs_stride,
+            const double *w, double *obs) {
+  return orc_rk4_t(m, y_re, y_im, 0.0, dt_fs, n_steps, obs_stride, w, obs);
 }

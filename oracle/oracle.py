@@ -14,6 +14,11 @@ Parity status of each function (against the paper, arXiv 1803.03498):
   coefficients   pinned (Matsubara sum rule, high-temperature limit, resonance rejection)
   rhs / rk4      pinned (dense Kronecker Liouvillian, textbook-gauge equivalence, unitary limit,
                  trace/Hermiticity invariants, thermal relaxation, RK4 order)
+  bath masks     pinned (dense Kronecker Liouvillian with diagonal V_b; the two-exciton space started
+                 in the one-exciton block equals the one-exciton model)
+  laser field    pinned (Rabi rotation of a two-level system by a resonant Gaussian pulse: closed form
+                 through the pulse area; two uncoupled sites in the two-exciton space: the product of
+                 two such rotations; a zero-amplitude field changes nothing)
   printed trajectories of the paper: parity unpinned (the paper prints figures only).
 """
 from __future__ import annotations
@@ -78,6 +83,14 @@ def lib():
         L.orc_record_len.restype = ctypes.c_int
         L.orc_rk4.argtypes = [vp, P(d), P(d), d, i64, i64, P(d), P(d)]
         L.orc_rk4.restype = ctypes.c_int
+        L.orc_rk4_t.argtypes = [vp, P(d), P(d), d, d, i64, i64, P(d), P(d)]
+        L.orc_rk4_t.restype = ctypes.c_int
+        L.orc_set_bath_mask.argtypes = [vp, P(u8)]
+        L.orc_set_bath_mask.restype = ctypes.c_int
+        L.orc_set_field.argtypes = [vp, P(d), d, d, d, d, d]
+        L.orc_set_field.restype = ctypes.c_int
+        L.orc_set_time.argtypes = [vp, d]
+        L.orc_set_time.restype = None
         _lib = L
     return _lib
 
@@ -130,6 +143,7 @@ class OracleModel:
     terminator: bool = True
     rescale: bool = True
     decomposition: str = "matsubara"  # or "pade"
+    bath_mask: np.ndarray | None = None  # [B, N] 0/1 diagonal of each V_b (None: |state><state|)
     _h: int = field(default=0, init=False, repr=False)
 
     def __post_init__(self):
@@ -151,6 +165,28 @@ class OracleModel:
         self._h = h
         self.n_ado = int(lib().orc_n_ado(h))
         self.M = int(lib().orc_n_modes(h))
+        if self.bath_mask is not None:
+            mk = np.ascontiguousarray(self.bath_mask, dtype=np.uint8)
+            assert mk.shape == (B, self.N)
+            if lib().orc_set_bath_mask(h, _ptr(mk, ctypes.c_uint8)):
+                raise ValueError("bath mask entries must be 0 or 1")
+
+    def set_field(self, mu_plus, amp_cm: float, t_center_fs: float, sigma_fs: float, phase: float = 0.0,
+                  detuning_cm: float = 0.0):
+        """H(t) = H - g(t) M+ - conj(g(t)) M+^T, g(t) = E0 exp(-(t - t_c)^2 / (2 sigma^2)) exp(-i (Delta t + phi));
+        mu_plus None removes the field."""
+        if mu_plus is None:
+            lib().orc_set_field(self._h, None, 0.0, 0.0, 1.0, 0.0, 0.0)
+            return
+        self._mup = np.ascontiguousarray(mu_plus, dtype=np.float64)
+        assert self._mup.shape == (self.N, self.N)
+        if lib().orc_set_field(self._h, _ptr(self._mup, ctypes.c_double), float(amp_cm), float(t_center_fs),
+                               float(sigma_fs), float(phase), float(detuning_cm)):
+            raise ValueError("sigma_fs must be > 0")
+
+    def set_time(self, t_fs: float):
+        """rhs() uses H(t_fs) from now on."""
+        lib().orc_set_time(self._h, float(t_fs))
 
     def __del__(self):
         if getattr(self, "_h", 0):
@@ -197,9 +233,10 @@ class OracleModel:
                            _ptr(im, ctypes.c_double), _ptr(ore, ctypes.c_double), _ptr(oim, ctypes.c_double))
         return ore, oim
 
-    def rk4(self, re: np.ndarray, im: np.ndarray, dt_fs: float, n_steps: int, obs_stride: int = 1, w=None):
-        """Classic RK4 in place on (re, im).  Returns records [n_rec, N+4]:
-        populations[N], trace re, trace im, correlation re, correlation im."""
+    def rk4(self, re: np.ndarray, im: np.ndarray, dt_fs: float, n_steps: int, obs_stride: int = 1, w=None,
+            t0: float = 0.0):
+        """Classic RK4 in place on (re, im) from time t0 (stage times t, t + h/2, t + h/2, t + h).
+        Returns records [n_rec, N+4]: populations[N], trace re, trace im, correlation re, correlation im."""
         assert re.flags.c_contiguous and im.flags.c_contiguous and re.dtype == np.float64
         rl = int(lib().orc_record_len(self._h))
         n_rec = (n_steps // obs_stride + 1) if obs_stride > 0 else 1
@@ -208,8 +245,8 @@ class OracleModel:
         if w is not None:
             w = np.ascontiguousarray(w, dtype=np.float64)
             wp = _ptr(w, ctypes.c_double)
-        rc = lib().orc_rk4(self._h, _ptr(re, ctypes.c_double), _ptr(im, ctypes.c_double), float(dt_fs), int(n_steps),
-                           int(obs_stride), wp, _ptr(obs, ctypes.c_double))
+        rc = lib().orc_rk4_t(self._h, _ptr(re, ctypes.c_double), _ptr(im, ctypes.c_double), float(t0), float(dt_fs),
+                             int(n_steps), int(obs_stride), wp, _ptr(obs, ctypes.c_double))
         if rc != 0:
             raise MemoryError("oracle RK4 workspace allocation failed")
         return obs

@@ -42,6 +42,7 @@ class System:
     K: int                        # modes per bath beyond the Drude mode (modes per bath = K + 1)
     D: int                        # hierarchy depth
     decomposition: str = "matsubara"  # expansion of the Bose function: "matsubara" or "pade"
+    bath_mask: np.ndarray | None = None  # [n_baths, N] 0/1: diagonal of V_b (None: |bath_state><bath_state|)
 
     @property
     def N(self) -> int:
@@ -119,6 +120,91 @@ def dipole_runs(sysm_sites: System, dip: np.ndarray, dt_fs: float, n_steps: int,
         re[:, 0] = w            # sigma_0(0) = mu_p^+ |0><0|
         out.append(Propagation(g, re, np.zeros_like(re), dt_fs, n_steps, w=w, tag=f"{tag}-dip{p}"))
     return out
+
+
+def two_exciton(sysm_sites: System, omega_ref: float | None = None):
+    """The system on the zero-, one- and two-exciton states of its N sites (section "Dipole operators
+    and rotational averaging": N_states = 1 + N + N (N - 1) / 2).  State 0 is the ground state,
+    state 1 + a has site a excited, and the pairs (a, b), a < b, follow in lexicographic order from
+    N + 1.  The sites are hard-core excitons: a pair has energy E_a + E_b and couples to the pair
+    (c, b) by J_ac (one excitation hops, the other stays).  Every excitation is counted from omega_ref
+    (default: the mean site energy), so singles are shifted by -omega_ref and pairs by -2 omega_ref:
+    the frame that rotates with a carrier at omega_ref.  The bath of site b couples through the site's
+    number operator: V_b is 1 at the single b and at every pair that contains b (bath_mask).
+    Returns (System, pairs)."""
+    n = sysm_sites.N
+    Hs = np.asarray(sysm_sites.H, dtype=float)
+    if omega_ref is None:
+        omega_ref = float(np.mean(np.diag(Hs)))
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    N = 1 + n + len(pairs)
+    idx = {p: 1 + n + k for k, p in enumerate(pairs)}
+    H = np.zeros((N, N))
+    H[1:n + 1, 1:n + 1] = Hs - omega_ref * np.eye(n)
+    for (a, b), i in idx.items():
+        H[i, i] = Hs[a, a] + Hs[b, b] - 2.0 * omega_ref
+        for (c, d), j in idx.items():
+            shared = {a, b} & {c, d}
+            if i != j and len(shared) == 1:
+                x = ({a, b} - shared).pop()
+                y = ({c, d} - shared).pop()
+                H[i, j] = Hs[x, y]
+    mask = np.zeros((len(sysm_sites.bath_state), N), np.uint8)
+    for k, site in enumerate(sysm_sites.bath_state):
+        mask[k, 1 + site] = 1
+        for (a, b), i in idx.items():
+            if site in (a, b):
+                mask[k, i] = 1
+    g = System(sysm_sites.name + " two-exciton", H, [1 + s for s in sysm_sites.bath_state],
+               list(sysm_sites.lambda_cm), list(sysm_sites.tau_fs), list(sysm_sites.T_K), sysm_sites.K,
+               sysm_sites.D, sysm_sites.decomposition, bath_mask=mask)
+    return g, pairs
+
+
+def two_exciton_dipole(n_sites: int, w) -> np.ndarray:
+    """M+ = e . mu^+ on the two-exciton space of n_sites (order of two_exciton) for the weights
+    w_a = e . d_a: site a is excited from the ground state (|a><0|) or on top of site b (|ab><b|)."""
+    pairs = [(a, b) for a in range(n_sites) for b in range(a + 1, n_sites)]
+    N = 1 + n_sites + len(pairs)
+    Mp = np.zeros((N, N))
+    for a in range(n_sites):
+        Mp[1 + a, 0] = w[a]
+    for k, (a, b) in enumerate(pairs):
+        i = 1 + n_sites + k
+        Mp[i, 1 + b] = w[a]
+        Mp[i, 1 + a] = w[b]
+    return Mp
+
+
+@dataclass
+class Pulse:
+    """A Gaussian laser pulse in the rotating-wave approximation (Eq. h-field-rwa with Eq. probe_pulse):
+    H(t) = H - g(t) M+ - conj(g(t)) M+^T, g(t) = amp exp(-(t - t_c)^2 / (2 sigma^2)) exp(-i (Delta t + phi)),
+    amp (the coupling mu E in cm^-1 for unit dipole weights) and the detuning Delta of the carrier
+    from the frame's reference frequency in cm^-1."""
+    mu_plus: np.ndarray
+    amp_cm: float
+    t_center_fs: float
+    sigma_fs: float
+    phase: float = 0.0
+    detuning_cm: float = 0.0
+
+
+def fmo_two_exciton(n_sites: int = 7, D: int = 3, seed: int = 1803002, dip_seed: int = 1803012, amp_cm: float = 60.0):
+    """The FMO-like system (first n_sites sites, K = 1) in the two-exciton space (29 states for
+    7 sites) under one Gaussian pump pulse (sigma 15 fs, centred at 40 fs, resonant, x-polarised),
+    from the ground state: returns (Propagation, Pulse)."""
+    pop, _ = fmo_like(seed, dip_seed)
+    s = pop.system
+    sub = System(f"fmo-like {n_sites} sites", np.asarray(s.H)[:n_sites, :n_sites], list(range(n_sites)),
+                 [35.0] * n_sites, [166.0] * n_sites, [77.0] * n_sites, K=1, D=D)
+    g, _ = two_exciton(sub)
+    dip = unit_dipoles(np.random.default_rng(dip_seed), 7)[:n_sites]
+    Mp = two_exciton_dipole(n_sites, dip[:, 0])
+    re = np.zeros((g.N, g.N))
+    re[0, 0] = 1.0
+    prop = Propagation(g, re, np.zeros_like(re), dt_fs=0.5, n_steps=200, tag=f"fmo-2x-{n_sites}")
+    return prop, Pulse(Mp, amp_cm, 40.0, 15.0)
 
 
 def site_positions(rng, n_sites, box_angstrom: float = 30.0):

@@ -7,7 +7,8 @@ from oracle.oracle import Bath, OracleModel
 def oracle_for(system, terminator=True, rescale=True):
     baths = [Bath(st, l, t, T) for st, l, t, T in zip(system.bath_state, system.lambda_cm, system.tau_fs, system.T_K)]
     return OracleModel(system.H, baths, K=system.K, D=system.D, terminator=terminator, rescale=rescale,
-                       decomposition=getattr(system, "decomposition", "matsubara"))
+                       decomposition=getattr(system, "decomposition", "matsubara"),
+                       bath_mask=getattr(system, "bath_mask", None))
 
 
 def oracle_start(m, rho_re, rho_im):

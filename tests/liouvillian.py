@@ -38,6 +38,16 @@ def build(H_rad, mode_state, gamma, c, lamnu, delta_state, D, terminator=True, r
     """H_rad: [N, N] complex, rad/fs.  Per mode: state, gamma, c (real), lamnu.  delta_state: [N]
     terminator coefficient summed per state.  Returns (L dense [nN^2, nN^2], tuples, index)."""
     N = H_rad.shape[0]
+    eye = np.eye(N)
+    mode_v = [eye[s] for s in mode_state]
+    bath_terms = [(delta_state[s], eye[s]) for s in range(N) if delta_state[s] != 0.0]
+    return build_general(H_rad, mode_v, gamma, c, lamnu, bath_terms, D, terminator, rescale, form)
+
+
+def build_general(H_rad, mode_v, gamma, c, lamnu, bath_terms, D, terminator=True, rescale=True, form="paper"):
+    """As build, for diagonal coupling operators: mode l couples through V_l = diag(mode_v[l]);
+    bath_terms: [(Delta_b, diagonal of V_b)], the terminator adds -Delta_b (V_b^x)^2."""
+    N = H_rad.shape[0]
     M = len(gamma)
     I = np.eye(N)
     tuples = enumerate_tuples(M, D)
@@ -45,38 +55,38 @@ def build(H_rad, mode_state, gamma, c, lamnu, delta_state, D, terminator=True, r
     nn = N * N
     L = np.zeros((len(tuples) * nn, len(tuples) * nn), dtype=complex)
     comm = np.kron(H_rad, I) - np.kron(I, H_rad.T)
-    P = [np.diag(np.eye(N)[s]) for s in range(N)]
-    Vx = [np.kron(P[s], I) - np.kron(I, P[s].T) for s in range(N)]
-    Vo = [np.kron(P[s], I) + np.kron(I, P[s].T) for s in range(N)]
+    P = [np.diag(np.asarray(v, dtype=float)) for v in mode_v]
+    Vx = [np.kron(P[l], I) - np.kron(I, P[l].T) for l in range(M)]
+    Vo = [np.kron(P[l], I) + np.kron(I, P[l].T) for l in range(M)]
     term = np.zeros((nn, nn), dtype=complex)
     if terminator:
-        for s in range(N):
-            if delta_state[s] != 0.0:
-                term += delta_state[s] * (Vx[s] @ Vx[s])
+        for delta, v in bath_terms:
+            Vb = np.diag(np.asarray(v, dtype=float))
+            X = np.kron(Vb, I) - np.kron(I, Vb.T)
+            term += delta * (X @ X)
     for t, u in index.items():
         blk = slice(u * nn, (u + 1) * nn)
         g = sum(t[l] * gamma[l] for l in range(M))
         L[blk, blk] += -1j * comm - g * np.eye(nn) - term
         for l in range(M):
-            s = mode_state[l]
             ac = abs(c[l])
             if sum(t) < D:
                 tp = list(t); tp[l] += 1
                 v = index[tuple(tp)]
                 if form == "paper":
                     f = np.sqrt((t[l] + 1) * ac) if (rescale and ac > 1e-300) else 1.0
-                    L[blk, v * nn:(v + 1) * nn] += 1j * f * Vx[s]
+                    L[blk, v * nn:(v + 1) * nn] += 1j * f * Vx[l]
                 else:
-                    L[blk, v * nn:(v + 1) * nn] += -1j * Vx[s]
+                    L[blk, v * nn:(v + 1) * nn] += -1j * Vx[l]
             if t[l] >= 1:
                 tm = list(t); tm[l] -= 1
                 v = index[tuple(tm)]
                 if form == "paper":
                     f = np.sqrt(t[l] / ac) if (rescale and ac > 1e-300) else float(t[l])
-                    L[blk, v * nn:(v + 1) * nn] += f * (1j * c[l] * Vx[s] + lamnu[l] * Vo[s])
+                    L[blk, v * nn:(v + 1) * nn] += f * (1j * c[l] * Vx[l] + lamnu[l] * Vo[l])
                 else:
                     ct = c[l] - 1j * lamnu[l]
-                    L[blk, v * nn:(v + 1) * nn] += -1j * t[l] * (ct * np.kron(P[s], I) - np.conj(ct) * np.kron(I, P[s].T))
+                    L[blk, v * nn:(v + 1) * nn] += -1j * t[l] * (ct * np.kron(P[l], I) - np.conj(ct) * np.kron(I, P[l].T))
     return L, tuples, index
 
 
