@@ -59,6 +59,17 @@ typedef struct heom_run heom_run;
  * (the 0-based form of the paper's l = (b-1)K + k + 1).
  * terminator: 1 adds the Matsubara terminator term of Eq. HEOM, 0 drops it.
  * rescale: 1 applies the ADO rescaling (sqrt((n+1)|c|) up, sqrt(n/|c|) down), 0 uses 1 and n.
+ * bath_mask (may be NULL): [n_baths][n_states] of 0/1; bath b then couples through the diagonal
+ *   V_b with 1 at every state whose entry is 1 -- in the two-exciton space (section "Dipole
+ *   operators and rotational averaging") the number operator of site b: its single-exciton state and
+ *   every pair that contains it.  V^x, V^x V^x and V^o keep their element-wise definitions; the
+ *   terminator then has the element rate T_ij = sum_b Delta_b (V_b,ii - V_b,jj)^2.  bath_state[b]
+ *   must still name a state of the bath (it labels the bath's modes in heom_bath_modes).
+ * time_dependent: 1 reserves a fourth state copy so that the run can take a laser field
+ *   (heom_run_set_field) and be propagated by classic four-copy RK4 with H(t) at each stage time.
+ * Runs with a bath_mask, with time_dependent = 1 or with more than 24 states (up to 32, e.g. the
+ * 29 states of a 7-site two-exciton space) use the general stage kernel; all others use the
+ * specialised ones.
  * All pointers are read during the call only (copied).
  */
 typedef struct {
@@ -74,6 +85,8 @@ typedef struct {
   int terminator;
   int rescale;
   int decomposition;       /* HEOM_MATSUBARA or HEOM_PADE */
+  const unsigned char *bath_mask; /* [n_baths * n_states] 0/1 diagonal of each V_b, or NULL */
+  int time_dependent;      /* 1: the run keeps a fourth state copy for a laser field */
 } heom_system;
 
 /* Expansion of the Bose function behind the bath modes (section "HEOM formalism"):
@@ -133,7 +146,7 @@ int heom_bath_modes(const heom_system *sys, double *gamma, double *c, double *la
 /*
  * heom_run_bytes -- device workspace bytes a run of this system, hierarchy and precision needs,
  * including room for max_records observable records.  The hierarchy's n_modes must equal
- * n_baths * (n_matsubara + 1).  Supported: 1 <= n_states <= 24.
+ * n_baths * (n_matsubara + 1).  Supported: 1 <= n_states <= 32 (above 24 on the general stage kernel).
  */
 int heom_run_bytes(const heom_system *sys, const heom_hier *h, int precision, int64_t max_records,
                    size_t *bytes);
@@ -151,7 +164,8 @@ int heom_run_bytes(const heom_system *sys, const heom_hier *h, int precision, in
  * heom_run_destroy.  Mixed-precision runs also own one library stream and two events: each stage's
  * small FP64 head launch runs there, forked from and joined back into the caller's stream, so that
  * it overlaps the body launch (work enqueued on the caller's stream stays ordered).  The bath
- * coefficients follow sys->decomposition (Matsubara or Pade).
+ * coefficients follow sys->decomposition (Matsubara or Pade).  Runs on the general stage kernel
+ * (bath_mask, time_dependent or more than 24 states) always use the matrix layout.
  */
 int heom_run_create(const heom_system *sys, const heom_hier *h, int precision, int64_t max_records,
                     const double *sigma0_re, const double *sigma0_im, const double *dip_w,
@@ -167,6 +181,31 @@ int heom_run_destroy(heom_run *r);
  * would overflow max_records), HEOM_E_CUDA.
  */
 int heom_propagate(heom_run *r, double dt_fs, int64_t n_steps, int64_t obs_stride);
+
+/*
+ * heom_run_set_field -- a laser field in the rotating-wave approximation (Eq. h-field-rwa with the
+ *   pulse of Eq. probe_pulse), seen from the frame that rotates at the reference frequency already
+ *   subtracted from each excitation in H:
+ *     H(t) = H - g(t) M+ - conj(g(t)) (M+)^T,
+ *     g(t) = amp_cm exp(-(t - t_center_fs)^2 / (2 sigma_fs^2)) exp(-i (detuning t + phase)),
+ *   with M+ the real polarisation-weighted dipole raising operator e . mu^+ (for example |a><0| and
+ *   |ab><b| with weights e . d_a in the two-exciton space), amp_cm the peak of dipole times field and
+ *   detuning_cm the carrier minus the reference frequency, both in cm^-1.  The run must have been
+ *   created with time_dependent = 1 (else HEOM_E_STATE).  From then on heom_propagate uses classic
+ *   four-copy RK4 with H at each stage time t, t + h/2, t + h/2, t + h (t counted from creation, the
+ *   time heom_run_info reports) and heom_rhs_eval uses H at the current time.  f == NULL removes
+ *   the field (Horner RK4 again).  A run with a field cannot join a batch (its graph would replay
+ *   fixed times).  Errors: HEOM_E_ARG (sigma_fs <= 0, NULL mu_plus), HEOM_E_STATE.
+ */
+typedef struct {
+  const double *mu_plus;   /* [n_states * n_states] M+, row-major, real */
+  double amp_cm;           /* peak coupling (dipole times field), cm^-1 */
+  double t_center_fs;      /* centre of the Gaussian envelope */
+  double sigma_fs;         /* its width: exp(-(t - t_c)^2 / (2 sigma^2)) */
+  double phase;            /* pulse phase, rad */
+  double detuning_cm;      /* carrier minus reference frequency, cm^-1 */
+} heom_field;
+int heom_run_set_field(heom_run *r, const heom_field *f);
 
 /* Length in doubles of one observable record: n_states populations Re sigma_0[a][a], then
  * Re Tr sigma_0, Im Tr sigma_0, Re C, Im C (C = sum_a w_a sigma_0[a][0], 0 without dip_w), then

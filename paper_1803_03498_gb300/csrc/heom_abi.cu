@@ -84,6 +84,12 @@ struct heom_run {
   bool cplx_h = false;
   bool herm = false;                 // every ADO Hermitian (Hermitian H and data; paper gauge)
   bool vec = false;                  // every ADO in the coherence block |a><0|: stored as its column 0
+  bool gen = false;                  // general stage kernel (bath masks, laser field, > 24 states)
+  std::vector<double> T;             // [n][n] terminator rate of each element (general kernel)
+  bool has_field = false;            // laser field set (heom_run_set_field): classic four-copy RK4
+  std::vector<double> mup;           // [n][n] M+
+  double famp = 0, ftc = 0, fsig = 1, fphase = 0, fdet = 0;  // rad/fs, fs, fs, rad, rad/fs
+  std::vector<double> Ht, Hit;       // H(t) of the current stage (general kernel)
   size_t copy_bytes = 0;             // bytes of one state copy (head + body, matrix layout)
   double bytes_full_y = 0, bytes_full_noy = 0, flops_full = 0;  // matrix-layout accounting
   VecRunDesc *desc_dev = nullptr;    // [8] stage arguments for batched column-0 launches
@@ -91,7 +97,7 @@ struct heom_run {
   std::vector<double> term;          // per state
   double max_rate = 0;               // D * max gamma
   // device
-  StateView y{}, zA{}, zB{};
+  StateView y{}, zA{}, zB{}, zC{};   // zC: RK4 accumulator of time-dependent runs
   int64_t *link_off = nullptr;       // [n_ado + 1]
   void *recs_head = nullptr;         // LinkRec<double>, ADOs u < u_split
   void *recs_body = nullptr;         // LinkRec<float or double>, ADOs u >= u_split
@@ -168,7 +174,7 @@ namespace {
 
 struct Layout {
   size_t off_loff, off_rh, off_rb, off_gsum, off_rec, off_w, off_cnt, off_desc;
-  size_t off_state[3];
+  size_t off_state[4];  // y, zA, zB, and (time-dependent runs) the RK4 accumulator
   size_t head_bytes, body_bytes;
   size_t total;
 };
@@ -178,8 +184,18 @@ inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 // The system alone (no hierarchy, no precision).
 int check_system_only(const heom_system *s) {
   if (!s) { set_error("NULL system"); return HEOM_E_ARG; }
-  if (s->n_states < 1 || s->n_states > kMaxStates) {
-    set_error("n_states must be in [1, 24]");
+  if (s->n_states < 1 || s->n_states > kGenMaxStates) {
+    set_error("n_states must be in [1, 32]");
+    return HEOM_E_ARG;
+  }
+  if (s->bath_mask)
+    for (int64_t e = 0; e < (int64_t)s->n_baths * s->n_states; ++e)
+      if (s->bath_mask[e] > 1) {
+        set_error("bath_mask entries must be 0 or 1");
+        return HEOM_E_ARG;
+      }
+  if (s->time_dependent != 0 && s->time_dependent != 1) {
+    set_error("time_dependent must be 0 or 1");
     return HEOM_E_ARG;
   }
   if (!s->H_re) { set_error("H_re is NULL"); return HEOM_E_ARG; }
@@ -279,15 +295,24 @@ static void pade_poles(int K, std::vector<double> &xi, std::vector<double> &eta)
 
 // Bath modes of Eq. HEOM (Drude-Lorentz, Omega = 0) in rad/fs: rates, real coefficients, lambda nu
 // of the Drude modes, coupled states, per-state terminator; gmax = the largest rate.
+// Diagonal of V_b: the bath's row of bath_mask, else 1 at bath_state[b].
+static double v_diag(const heom_system *sys, int b, int i) {
+  if (sys->bath_mask) return (double)sys->bath_mask[(size_t)b * sys->n_states + i];
+  return sys->bath_state[b] == i ? 1.0 : 0.0;
+}
+
+// Per mode: gamma, c, lambda nu (k = 0), the bath's labelling state; per state the terminator rate
+// sum_b Delta_b V_b,ii; per bath Delta_b (0 without the terminator) in *dbath if given.
 static int compute_modes(const heom_system *sys, std::vector<double> &gam, std::vector<double> &cc,
                          std::vector<double> &lnu, std::vector<int> &mstate, std::vector<double> &term,
-                         double *gmax) {
+                         double *gmax, std::vector<double> *dbath = nullptr) {
   const int B = sys->n_baths, K = sys->n_matsubara, M = B * (K + 1);
   gam.assign(M, 0.0);
   cc.assign(M, 0.0);
   lnu.assign(M, 0.0);
   mstate.assign(M, 0);
   term.assign(sys->n_states, 0.0);
+  if (dbath) dbath->assign(B, 0.0);
   *gmax = 0;
   std::vector<double> xi, eta;
   if (sys->decomposition == HEOM_PADE) pade_poles(K, xi, eta);
@@ -327,32 +352,57 @@ static int compute_modes(const heom_system *sys, std::vector<double> &gam, std::
       csum += cc[l] / gam[l];
       *gmax = std::max(*gmax, gam[l]);
     }
-    if (sys->terminator) term[sys->bath_state[b]] += 2.0 * lam / (beta * nu) - csum;
+    if (sys->terminator) {
+      const double delta = 2.0 * lam / (beta * nu) - csum;
+      for (int i = 0; i < sys->n_states; ++i) term[i] += delta * v_diag(sys, b, i);
+      if (dbath) (*dbath)[b] = delta;
+    }
   }
   return HEOM_OK;
 }
 
-// Valid links (up and down) of the ADOs [u_lo, u_hi).
-int64_t count_links(const Hierarchy &h, int64_t u_lo, int64_t u_hi) {
+// Link records of the ADOs [u_lo, u_hi): one per valid link (up and down) and coupled state; mult[l]
+// = states of mode l's V (1 for a projector; nullptr: all 1).
+int64_t count_links(const Hierarchy &h, int64_t u_lo, int64_t u_hi, const std::vector<int> *mult = nullptr) {
   int64_t k = 0;
   for (int64_t u = u_lo; u < u_hi; ++u)
-    for (int l = 0; l < h.M; ++l) k += (h.plus[(size_t)u * h.M + l] >= 0) + (h.minus[(size_t)u * h.M + l] >= 0);
+    for (int l = 0; l < h.M; ++l)
+      k += ((h.plus[(size_t)u * h.M + l] >= 0) + (h.minus[(size_t)u * h.M + l] >= 0)) * (mult ? (*mult)[l] : 1);
   return k;
+}
+
+// States coupled by each mode's V (the bath's mask row count, 1 without a mask).
+std::vector<int> mode_mult(const heom_system *sys) {
+  const int K1 = sys->n_matsubara + 1;
+  std::vector<int> m((size_t)sys->n_baths * K1, 1);
+  if (sys->bath_mask)
+    for (int b = 0; b < sys->n_baths; ++b) {
+      int c = 0;
+      for (int i = 0; i < sys->n_states; ++i) c += sys->bath_mask[(size_t)b * sys->n_states + i];
+      for (int k = 0; k < K1; ++k) m[(size_t)b * K1 + k] = c;
+    }
+  return m;
+}
+
+// Runs the specialised kernels do not cover: several states per bath, a laser field, > 24 states.
+bool needs_general(const heom_system *sys) {
+  return sys->bath_mask != nullptr || sys->time_dependent || sys->n_states > kMaxStates;
 }
 
 int split_of(const Hierarchy &h, int precision) {
   return (precision == HEOM_FP64) ? 0 : (int)std::min<int64_t>(h.n, h.level_off[std::min(2, h.D + 1)]);
 }
 
-Layout make_layout(int n, const Hierarchy &h, int u_split, int precision, int64_t max_records, int *Ep) {
+Layout make_layout(int n, const Hierarchy &h, int u_split, int precision, int64_t max_records, int *Ep,
+                   const std::vector<int> *mult = nullptr, int copies = 3) {
   Layout L{};
   const int64_t E = (int64_t)n * n;
   const int64_t n_ado = h.n;
   const size_t be = (precision == HEOM_FP64) ? sizeof(double2) : sizeof(float2);
   const size_t rb = (precision == HEOM_FP64) ? sizeof(LinkRec<double>) : sizeof(LinkRec<float>);
   *Ep = (int)((be == sizeof(float2) && (E & 1)) ? E + 1 : E);
-  const int64_t lh = count_links(h, 0, u_split);
-  const int64_t lb = h.n_links - lh;
+  const int64_t lh = count_links(h, 0, u_split, mult);
+  const int64_t lb = (mult ? count_links(h, 0, h.n, mult) : h.n_links) - lh;
   size_t o = 0;
   L.off_loff = o; o = al(o + (size_t)(n_ado + 1) * sizeof(int64_t));
   L.off_rh = o; o = al(o + (size_t)lh * sizeof(LinkRec<double>));
@@ -364,7 +414,7 @@ Layout make_layout(int n, const Hierarchy &h, int u_split, int precision, int64_
   L.off_desc = o; o = al(o + 8 * sizeof(VecRunDesc));  // batched column-0 stage arguments (4 stages x 2)
   L.head_bytes = al((size_t)u_split * E * sizeof(double2));
   L.body_bytes = al((size_t)(n_ado - u_split) * *Ep * be);
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < copies; ++c) {
     L.off_state[c] = o;
     o = al(o + L.head_bytes + L.body_bytes);
   }
@@ -407,7 +457,9 @@ extern "C" int heom_run_bytes(const heom_system *sys, const heom_hier *h, int pr
   if (rc) return rc;
   if (!bytes || max_records < 0) { set_error("heom_run_bytes: bad output pointer or max_records"); return HEOM_E_ARG; }
   int Ep;
-  Layout L = make_layout(sys->n_states, h->h, split_of(h->h, precision), precision, max_records, &Ep);
+  const std::vector<int> mult = mode_mult(sys);
+  Layout L = make_layout(sys->n_states, h->h, split_of(h->h, precision), precision, max_records, &Ep,
+                         sys->bath_mask ? &mult : nullptr, sys->time_dependent ? 4 : 3);
   *bytes = L.total;
   return HEOM_OK;
 }
@@ -469,7 +521,10 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   r->u_split = split_of(h, precision);
   r->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   r->max_records = max_records;
-  Layout L = make_layout(n, h, r->u_split, precision, max_records, &r->Ep);
+  r->gen = needs_general(sys);
+  const std::vector<int> mult = mode_mult(sys);
+  const std::vector<int> *mp = sys->bath_mask ? &mult : nullptr;  // records per link: 1 without a mask
+  Layout L = make_layout(n, h, r->u_split, precision, max_records, &r->Ep, mp, sys->time_dependent ? 4 : 3);
   r->E = n * n;
   if (workspace_bytes < L.total) {
     delete r;
@@ -513,7 +568,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   // ---- coherence block (linear-absorption runs): state 0 without a bath, no H element between state
   // 0 and the others, rho(0) supported on column 0 below the diagonal; every ADO then stays of the
   // form sum_a x_a |a><0| and is stored and propagated as that column (vec_kernel.cuh)
-  r->vec = n >= 2 && !r->cplx_h;
+  r->vec = n >= 2 && !r->cplx_h && !r->gen;
   for (int b = 0; b < B && r->vec; ++b) r->vec = sys->bath_state[b] != 0;
   for (int a = 1; a < n && r->vec; ++a) r->vec = sys->H_re[a] == 0.0 && sys->H_re[a * n] == 0.0;
   for (int i = 0; i < n && r->vec; ++i)
@@ -522,14 +577,25 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   if (r->vec) r->herm = false;
 
   // ---- bath modes of Eq. HEOM (Drude-Lorentz, Omega = 0), terminator and rescaling
-  std::vector<double> gam, cc, lnu;
+  std::vector<double> gam, cc, lnu, dbath;
   std::vector<int> mstate;
   double gmax = 0;
-  if (compute_modes(sys, gam, cc, lnu, mstate, r->term, &gmax)) {
+  if (compute_modes(sys, gam, cc, lnu, mstate, r->term, &gmax, &dbath)) {
     delete r;
     return HEOM_E_ARG;
   }
   r->max_rate = D * gmax;
+  if (r->gen) {  // terminator rate of element (i, j): sum_b Delta_b (V_b,ii - V_b,jj)^2
+    r->T.assign((size_t)n * n, 0.0);
+    for (int b = 0; b < B; ++b)
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          const double d = v_diag(sys, b, i) - v_diag(sys, b, j);
+          r->T[(size_t)i * n + j] += dbath[b] * d * d;
+        }
+    r->Ht = r->H;
+    r->Hit = r->Hi;
+  }
 
   // ---- rescaling factors s+_l(n), s-_l(n) (section "HEOM formalism", ADO rescaling)
   std::vector<double> sp((size_t)M * (D + 1)), sm((size_t)M * (D + 1));
@@ -550,10 +616,11 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   std::vector<LinkRec<float>> rbf;
   const bool body_fp64 = precision == HEOM_FP64;
   try {
-    const int64_t lh = count_links(h, 0, r->u_split);
+    const int64_t lh = count_links(h, 0, r->u_split, mp);
+    const int64_t lt = mp ? count_links(h, 0, h.n, mp) : h.n_links;
     rh.reserve(lh);
-    if (body_fp64) rbd.reserve(h.n_links - lh);
-    else rbf.reserve(h.n_links - lh);
+    if (body_fp64) rbd.reserve(lt - lh);
+    else rbf.reserve(lt - lh);
   } catch (...) {
     delete r;
     set_error("host allocation failed (link records)");
@@ -586,7 +653,13 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
           re = f * lnu[l];
           im = f * cc[l];
         }
-        pend.push_back(Pending{v, mstate[l], re, im});
+        if (!sys->bath_mask) {
+          pend.push_back(Pending{v, mstate[l], re, im});
+        } else {  // one record per state of the bath's V (same coefficient)
+          const int b = l / (K + 1);
+          for (int st = 0; st < n; ++st)
+            if (sys->bath_mask[(size_t)b * n + st]) pend.push_back(Pending{v, st, re, im});
+        }
       }
     }
     // records of one ADO ordered by state (the kernels give all records of a state to one lane);
@@ -650,6 +723,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
   r->y = view_at(base, L, 0);
   r->zA = view_at(base, L, 1);
   r->zB = view_at(base, L, 2);
+  if (sys->time_dependent) r->zC = view_at(base, L, 3);
 
   std::vector<double> w(n, 0.0);
   if (dip_w) for (int i = 0; i < n; ++i) w[i] = dip_w[i];
@@ -793,7 +867,56 @@ static int launch_body(heom_run *r, StageCommon c, double ch, cudaStream_t s) {
   return HEOM_OK;
 }
 
+// H(t) of a run with a laser field (Eq. h-field-rwa in the rotating frame):
+// H - g M+ - conj(g) (M+)^T, g = amp exp(-(t - t_c)^2 / (2 sigma^2)) exp(-i (Delta t + phi)).
+static void field_H(heom_run *r, double t) {
+  const int n = r->n;
+  const double x = (t - r->ftc) / r->fsig;
+  const double env = r->famp * std::exp(-0.5 * x * x);
+  const double ph = r->fdet * t + r->fphase;
+  const double gr = env * std::cos(ph), gi = -env * std::sin(ph);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double a = r->mup[(size_t)i * n + j], b = r->mup[(size_t)j * n + i];
+      r->Ht[(size_t)i * n + j] = r->H[(size_t)i * n + j] - gr * (a + b);
+      r->Hit[(size_t)i * n + j] = r->Hi[(size_t)i * n + j] - gi * a + gi * b;
+    }
+}
+
+// One stage on the general kernel: out1 = base1 + c1 L zin and, if out2 is set, out2 = base2 + c2 L zin,
+// with H(t) from r->Ht (field) or the constant H.
+static int run_stage_gen(heom_run *r, StateView zin, StateView b1, StateView o1, double c1, StateView b2, StateView o2,
+                         double c2) {
+  StageCommon c = common_for(r, zin, b1, o1);
+  const double *H = r->has_field ? r->Ht.data() : r->H.data();
+  const double *Hi = r->has_field ? r->Hit.data() : r->Hi.data();
+  const bool fp64 = r->precision == HEOM_FP64;
+  cudaStream_t hs = r->stream;
+  int rc;
+  if (!fp64) {  // FP64 head (levels 0, 1) on the side stream
+    hs = fork_head(r);
+    StageCommon ch = c;
+    ch.u_begin = 0;
+    ch.u_end = r->u_split;
+    ch.occ_pct = r->sched[1].occupancy_pct;
+    if (launch_stage_gen(2, ch, b2, o2, c1, c2, H, Hi, r->T.data(), hs, r->sm_count)) return HEOM_E_CUDA;
+    ++r->launches;
+  }
+  c.u_begin = fp64 ? 0 : r->u_split;
+  c.u_end = (int)r->n_ado;
+  c.occ_pct = r->sched[0].occupancy_pct;
+  if (c.u_end > c.u_begin) {
+    if ((rc = timed_begin(r))) return rc;
+    if (launch_stage_gen(fp64 ? 0 : 1, c, b2, o2, c1, c2, H, Hi, r->T.data(), r->stream, r->sm_count))
+      return HEOM_E_CUDA;
+    ++r->launches;
+    if ((rc = timed_end(r, r->bytes_stage_y))) return rc;
+  }
+  return join_head(r, hs);
+}
+
 static int run_stage(heom_run *r, StateView zin, StateView y, StateView out, double ch) {
+  if (r->gen) return run_stage_gen(r, zin, y, out, ch, StateView{nullptr, nullptr}, StateView{nullptr, nullptr}, 0.0);
   const StageCommon c = common_for(r, zin, y, out);
   const bool same_y = (y.head == zin.head && y.body == zin.body);
   const bool no_y = (y.head == nullptr && y.body == nullptr);
@@ -935,6 +1058,7 @@ void reschedule_cached(heom_run *r) {
 
 // The schedule of each part of a new run: the cache, else the tuner (if on), else the default.
 int schedule_new_run(heom_run *r) {
+  if (r->gen) return HEOM_OK;  // the general kernel keeps the default schedule
   const int reps = g_autotune.load();
   for (int part = 0; part < (r->precision == HEOM_FP64 ? 1 : 2); ++part) {
     heom_schedule s{100, 1};
@@ -967,6 +1091,10 @@ extern "C" int heom_tune(heom_run *r, int part, int reps, heom_schedule *tried, 
   if (!r || reps < 1 || part < 0 || part > 1 || (part == 1 && r->precision == HEOM_FP64) || cap < 0) {
     set_error("heom_tune: need a run, reps >= 1, part 0 or 1 (1 only with an FP64 head), cap >= 0");
     return HEOM_E_ARG;
+  }
+  if (r->gen) {
+    set_error("heom_tune: runs on the general stage kernel keep the default schedule");
+    return HEOM_E_STATE;
   }
   std::vector<heom_schedule> t;
   std::vector<double> m;
@@ -1070,7 +1198,27 @@ extern "C" int heom_propagate(heom_run *r, double dt_fs, int64_t n_steps, int64_
   }
   const double h = dt_fs;
   StateView none{nullptr, nullptr};
-  (void)none;
+  if (r->has_field) {
+    // classic four-copy RK4 of the time-dependent L(t): k_s = L(t_s) X_s, X_{s+1} = y + a h k_s,
+    // acc (zC) = y + h (k1 + 2 k2 + 2 k3) / 6, y = acc + h k4 / 6
+    const double t0 = r->t_fs;
+    for (int64_t s = 0; s < n_steps; ++s) {
+      const double t = t0 + (double)s * h;
+      int rc;
+      field_H(r, t);
+      if ((rc = run_stage_gen(r, r->y, r->y, r->zA, h / 2, r->y, r->zC, h / 6))) return rc;
+      field_H(r, t + h / 2);
+      if ((rc = run_stage_gen(r, r->zA, r->y, r->zB, h / 2, r->zC, r->zC, h / 3))) return rc;
+      if ((rc = run_stage_gen(r, r->zB, r->y, r->zA, h, r->zC, r->zC, h / 3))) return rc;
+      field_H(r, t + h);
+      if ((rc = run_stage_gen(r, r->zA, r->zC, r->y, h / 6, none, none, 0.0))) return rc;
+      ++r->steps_done;
+      r->t_fs = t0 + (double)(s + 1) * h;
+      if (obs_stride > 0 && r->steps_done % obs_stride == 0)
+        if ((rc = enqueue_record(r))) return rc;
+    }
+    return HEOM_OK;
+  }
   for (int64_t s = 0; s < n_steps; ++s) {
     int rc;
     if ((rc = run_stage(r, r->y, r->y, r->zA, h / 4))) return rc;
@@ -1236,6 +1384,7 @@ extern "C" int heom_get_sigma0(heom_run *r, double *re, double *im) { return heo
 extern "C" int heom_rhs_eval(heom_run *r, int64_t u0, int64_t count, double *re, double *im) {
   if (!r) { set_error("heom_rhs_eval: NULL run"); return HEOM_E_ARG; }
   StateView none{nullptr, nullptr};
+  if (r->has_field) field_H(r, r->t_fs);  // L at the current time
   int rc = run_stage(r, r->y, none, r->zA, 1.0);
   if (rc) return rc;
   cudaError_t e = cudaStreamSynchronize(r->stream);
@@ -1255,6 +1404,33 @@ extern "C" int heom_run_info(const heom_run *r, int64_t *n_ado, int *n_states, i
 }
 
 extern "C" int heom_run_layout(const heom_run *r) { return r ? (r->vec ? 1 : 0) : -1; }
+
+extern "C" int heom_run_set_field(heom_run *r, const heom_field *f) {
+  if (!r) { set_error("heom_run_set_field: NULL run"); return HEOM_E_ARG; }
+  if (!r->zC.head && !r->zC.body) {
+    set_error("heom_run_set_field: the run was created without time_dependent = 1");
+    return HEOM_E_STATE;
+  }
+  if (!f) {
+    r->has_field = false;
+    return HEOM_OK;
+  }
+  if (!f->mu_plus || !(f->sigma_fs > 0)) {
+    set_error("heom_run_set_field: need mu_plus and sigma_fs > 0");
+    return HEOM_E_ARG;
+  }
+  const int n = r->n;
+  r->mup.assign(f->mu_plus, f->mu_plus + (size_t)n * n);
+  r->famp = kCmToRadFs * f->amp_cm;
+  r->ftc = f->t_center_fs;
+  r->fsig = f->sigma_fs;
+  r->fphase = f->phase;
+  r->fdet = kCmToRadFs * f->detuning_cm;
+  r->Ht.assign((size_t)n * n, 0.0);
+  r->Hit.assign((size_t)n * n, 0.0);
+  r->has_field = true;
+  return HEOM_OK;
+}
 
 extern "C" int64_t heom_run_launches(const heom_run *r) { return r ? r->launches : -1; }
 
@@ -1421,6 +1597,10 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
       return HEOM_E_ARG;
     }
     if (runs[i]->timing) { set_error("heom_batch_create: switch timing off on every run first"); return HEOM_E_STATE; }
+    if (runs[i]->has_field) {
+      set_error("heom_batch_create: a run with a laser field cannot be batched (its graph would replay fixed times)");
+      return HEOM_E_ARG;
+    }
   }
   heom_batch *b = new (std::nothrow) heom_batch;
   if (!b) { set_error("host allocation failed"); return HEOM_E_NOMEM; }

@@ -148,6 +148,23 @@ HEOM_DECLARE_LAUNCH(launch_stage_head_c)
 HEOM_DECLARE_LAUNCH(launch_stage_head_d)
 #undef HEOM_DECLARE_LAUNCH
 
+// General stage kernel (gen_kernel.cuh): bath couplings with several states, a time-dependent H and
+// up to kGenMaxStates states.  out1 (c.out) = base1 (c.y) + c1 L zin; out2 = base2 + c2 L zin when
+// out2 is set.  H, Hi, T: host arrays [n][n] (H(t) - h0 and Im H(t) in rad/fs; T_ij the terminator
+// rate of element (i, j)).  kind as launch_stage_vec.
+constexpr int kGenMaxStates = 32;
+template <typename CT>
+struct GenArgs {
+  StageCommon c;
+  StateView base2, out2;
+  CT c1, c2;
+  CT H[kGenMaxStates * kGenMaxStates];
+  CT Hi[kGenMaxStates * kGenMaxStates];
+  CT T[kGenMaxStates * kGenMaxStates];
+};
+int launch_stage_gen(int kind, const StageCommon &c, StateView base2, StateView out2, double c1, double c2,
+                     const double *H, const double *Hi, const double *T, cudaStream_t st, int sm_count);
+
 // precision: 0 = FP64 (compute and storage double), 1 = mixed body (float, float), 2 = mixed head
 // (compute double, body storage float).
 int launch_stage(int precision, const StageCommon &c, double ch, const double *term, const double *H,

@@ -27,7 +27,7 @@ ABI_SYMBOLS = [
     "heom_run_launches", "heom_run_set_timing", "heom_run_kernel_time", "heom_propagate_static",
     "heom_batch_create", "heom_batch_launch", "heom_batch_destroy", "heom_bath_modes", "heom_run_layout",
     "heom_schedule_candidates", "heom_tune", "heom_set_autotune", "heom_get_schedule", "heom_set_schedule",
-    "heom_tune_cache_clear", "heom_batch_schedule", "heom_set_default_schedule",
+    "heom_tune_cache_clear", "heom_batch_schedule", "heom_set_default_schedule", "heom_run_set_field",
 ]
 MATSUBARA, PADE = 0, 1
 DECOMPOSITIONS = {"matsubara": MATSUBARA, "pade": PADE}
@@ -53,6 +53,19 @@ class _System(ctypes.Structure):
         ("terminator", ctypes.c_int),
         ("rescale", ctypes.c_int),
         ("decomposition", ctypes.c_int),
+        ("bath_mask", ctypes.POINTER(ctypes.c_uint8)),
+        ("time_dependent", ctypes.c_int),
+    ]
+
+
+class _Field(ctypes.Structure):
+    _fields_ = [
+        ("mu_plus", ctypes.POINTER(ctypes.c_double)),
+        ("amp_cm", ctypes.c_double),
+        ("t_center_fs", ctypes.c_double),
+        ("sigma_fs", ctypes.c_double),
+        ("phase", ctypes.c_double),
+        ("detuning_cm", ctypes.c_double),
     ]
 
 
@@ -111,6 +124,7 @@ def load():
     L.heom_set_schedule.argtypes = [vp, i, P(S)]
     L.heom_tune_cache_clear.argtypes = []
     L.heom_set_default_schedule.argtypes = [i, P(S)]
+    L.heom_run_set_field.argtypes = [vp, P(_Field)]
     L.heom_batch_schedule.argtypes = [vp, i, i, P(S), P(i)]
     for name in ABI_SYMBOLS:
         if name not in ("heom_last_error", "heom_run_launches"):
@@ -161,7 +175,7 @@ class Hierarchy:
 class _SysArgs:
     """Keeps the numpy arrays behind a heom_system alive."""
 
-    def __init__(self, system, terminator=True, rescale=True):
+    def __init__(self, system, terminator=True, rescale=True, time_dependent=False):
         H = np.asarray(system.H)
         self.H_re = np.ascontiguousarray(H.real, dtype=np.float64)
         self.H_im = np.ascontiguousarray(H.imag, dtype=np.float64) if np.iscomplexobj(H) else None
@@ -182,6 +196,10 @@ class _SysArgs:
         s.terminator = int(bool(terminator))
         s.rescale = int(bool(rescale))
         s.decomposition = DECOMPOSITIONS[getattr(system, "decomposition", "matsubara")]
+        mask = getattr(system, "bath_mask", None)
+        self.mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        s.bath_mask = None if self.mask is None else self.mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        s.time_dependent = int(bool(time_dependent))
         self.s = s
 
 
@@ -228,8 +246,9 @@ def bath_modes(system, terminator=True):
     return {"gamma": g, "c": c, "lamnu": ln, "mode_state": ms, "term": term}
 
 
-def run_bytes(system, hier: Hierarchy, precision="fp64", max_records=1, terminator=True, rescale=True) -> int:
-    sa = _SysArgs(system, terminator, rescale)
+def run_bytes(system, hier: Hierarchy, precision="fp64", max_records=1, terminator=True, rescale=True,
+              time_dependent=False) -> int:
+    sa = _SysArgs(system, terminator, rescale, time_dependent)
     b = ctypes.c_size_t()
     _check(load().heom_run_bytes(ctypes.byref(sa.s), hier._h, PRECISIONS[precision], int(max_records), ctypes.byref(b)))
     return int(b.value)
@@ -239,14 +258,15 @@ class Run:
     """One propagation (heom_run_create) on a torch-allocated device workspace and torch stream."""
 
     def __init__(self, system, rho0_re, rho0_im=None, precision="fp64", w=None, max_records=1024,
-                 terminator=True, rescale=True, hier: Hierarchy | None = None, stream=None, workspace=None):
+                 terminator=True, rescale=True, hier: Hierarchy | None = None, stream=None, workspace=None,
+                 time_dependent=False):
         import torch
 
         L = load()
         self.system = system
         self.hier = hier if hier is not None else Hierarchy(system.n_modes, system.D)
         self.precision = precision
-        self._sa = _SysArgs(system, terminator, rescale)
+        self._sa = _SysArgs(system, terminator, rescale, time_dependent)
         nbytes = ctypes.c_size_t()
         _check(L.heom_run_bytes(ctypes.byref(self._sa.s), self.hier._h, PRECISIONS[precision], int(max_records),
                                 ctypes.byref(nbytes)))
@@ -272,6 +292,17 @@ class Run:
     def layout(self) -> int:
         """0: ADOs stored as N x N matrices; 1: as their column 0 (coherence block)."""
         return int(load().heom_run_layout(self._r))
+
+    def set_field(self, pulse):
+        """heom_run_set_field: a Gaussian RWA pulse (workloads.Pulse or any object with mu_plus, amp_cm,
+        t_center_fs, sigma_fs, phase, detuning_cm); None removes it.  Needs time_dependent=True."""
+        if pulse is None:
+            _check(load().heom_run_set_field(self._r, None))
+            return
+        self._mup = np.ascontiguousarray(pulse.mu_plus, dtype=np.float64)
+        f = _Field(_dp(self._mup), float(pulse.amp_cm), float(pulse.t_center_fs), float(pulse.sigma_fs),
+                   float(getattr(pulse, "phase", 0.0)), float(getattr(pulse, "detuning_cm", 0.0)))
+        _check(load().heom_run_set_field(self._r, ctypes.byref(f)))
 
     def propagate(self, dt_fs: float, n_steps: int, obs_stride: int = 0):
         _check(load().heom_propagate(self._r, float(dt_fs), int(n_steps), int(obs_stride)))

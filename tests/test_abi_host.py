@@ -91,8 +91,8 @@ def test_run_bytes_and_argument_errors(lib):
     bad = wl.System("bad", p.system.H, [0, 5], [35.0] * 2, [50.0] * 2, [300.0] * 2, K=0, D=4)
     with pytest.raises(heom.HeomError):
         heom.run_bytes(bad, h, "fp64", 1)
-    # too many states
-    H = np.eye(25)
+    # too many states (the general kernel covers up to 32)
+    H = np.eye(33)
     bad = wl.System("big", H, [0], [35.0], [50.0], [300.0], K=0, D=1)
     with pytest.raises(heom.HeomError):
         heom.run_bytes(bad, heom.Hierarchy(1, 1), "fp64", 1)
@@ -118,3 +118,27 @@ def test_schedule_candidates_and_autotune_switch(lib):
     with pytest.raises(heom.HeomError) as ei:
         heom.set_default_schedule(0, (100, 3))
     assert ei.value.code == heom.HEOM_E_ARG
+
+
+def test_general_runs_bytes_and_mask_checks(lib):
+    """Runs on the general kernel: the records per link grow with the states of each V_b, a fourth
+    state copy is reserved for time-dependent runs, and bath_mask entries are checked."""
+    prop, _ = wl.fmo_two_exciton(n_sites=4, D=2)
+    s = prop.system
+    h = heom.Hierarchy(s.n_modes, s.D)
+    assert s.N == 11
+    b3 = heom.run_bytes(s, h, "fp64", 4)
+    b4 = heom.run_bytes(s, h, "fp64", 4, time_dependent=True)
+    assert b4 - b3 >= h.n_ado * s.N * s.N * 16  # one more FP64 copy
+    plain = wl.System("no mask", s.H, s.bath_state, s.lambda_cm, s.tau_fs, s.T_K, K=s.K, D=s.D)
+    # each site's V has 1 + 3 states here (its single and the three pairs with it): 4 records per link
+    links = int(np.sum(h.export()[1] >= 0) + np.sum(h.export()[2] >= 0))
+    assert b3 - heom.run_bytes(plain, h, "fp64", 4) >= 3 * links * 32
+    bad = wl.System("bad", s.H, s.bath_state, s.lambda_cm, s.tau_fs, s.T_K, K=s.K, D=s.D,
+                    bath_mask=np.full_like(s.bath_mask, 2))
+    with pytest.raises(heom.HeomError) as ei:
+        heom.run_bytes(bad, h, "fp64", 1)
+    assert ei.value.code == heom.HEOM_E_ARG and "bath_mask" in lib.heom_last_error().decode()
+    g7, _ = wl.fmo_two_exciton(n_sites=7, D=1)
+    assert g7.system.N == 29
+    heom.run_bytes(g7.system, heom.Hierarchy(g7.system.n_modes, 1), "fp32_mixed", 1)
