@@ -18,8 +18,9 @@
 // (column reads conflict-free, row reads broadcast); H, Im H and T sit in shared memory once per
 // CTA.  The commutator, decay and terminator go to a result tile R that lane j writes in column j;
 // the row parts of the links also land in column j of R (lane j loads v_sj, coalesced), the column
-// parts in row i of a second tile C (lane i loads v_is), so no element is written by two lanes and
-// no synchronisation is needed between records.  out = base + c (R + C).
+// parts in row i of a second tile C (lane i loads v_is; C reuses the input tile's buffer), so no
+// element is written by two lanes and no synchronisation is needed between records.  The records of
+// an ADO load 32 at a time, one per lane, and reach every lane by shuffles.  out = base + c (R + C).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -130,20 +131,29 @@ __global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_
     for (int e = lane; e < E; e += 32) Z[e] = C2{0, 0};  // Z becomes the column-part tile
     __syncwarp();
     const int64_t lo = c.link_off[u], hi = c.link_off[u + 1];
-    for (int64_t t = lo; t < hi; ++t) {
-      const LinkRec<CT> rec = recs[t - rbase];
-      const int s = rec.s & kRecStateMask;
-      if (lj) {
-        // row part: element (s, j) += R v_sj (lane j, column j of R)
-        const C2 vs = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, rec.v, s * N + j);
-        C2 &rs = R[s * N + j];
-        rs.x += rec.re * vs.x - rec.im * vs.y;
-        rs.y += rec.re * vs.y + rec.im * vs.x;
-        // column part: element (i = j, s) += conj(R) v_js (lane j, row j of Z)
-        const C2 vc = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, rec.v, j * N + s);
-        C2 &zc = Z[j * N + s];
-        zc.x += rec.re * vc.x + rec.im * vc.y;
-        zc.y += rec.re * vc.y - rec.im * vc.x;
+    // the records of a window of 32 load together, one per lane, and reach every lane by shuffles;
+    // the neighbour loads of 4 records are in flight together (unrolled)
+    for (int64_t base = lo; base < hi; base += 32) {
+      const int cnt = (int)min((int64_t)32, hi - base);
+      LinkRec<CT> mine{};
+      if (lane < cnt) mine = recs[base + lane - rbase];
+#pragma unroll 4
+      for (int k = 0; k < cnt; ++k) {
+        const int v = __shfl_sync(0xffffffffu, mine.v, k);
+        const int s = __shfl_sync(0xffffffffu, mine.s, k) & kRecStateMask;
+        const CT rre = __shfl_sync(0xffffffffu, mine.re, k), rim = __shfl_sync(0xffffffffu, mine.im, k);
+        if (lj) {
+          // row part: element (s, j) += R v_sj (lane j, column j of R)
+          const C2 vs = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, v, s * N + j);
+          // column part: element (i = j, s) += conj(R) v_js (lane j, row j of Z)
+          const C2 vc = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, v, j * N + s);
+          C2 &rs = R[s * N + j];
+          rs.x += rre * vs.x - rim * vs.y;
+          rs.y += rre * vs.y + rim * vs.x;
+          C2 &zc = Z[j * N + s];
+          zc.x += rre * vc.x + rim * vc.y;
+          zc.y += rre * vc.y - rim * vc.x;
+        }
       }
     }
     __syncwarp();
