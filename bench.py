@@ -145,14 +145,17 @@ def _barrier(ws):
         dist.barrier()
 
 
-def time_gpu(prop, precision, steps, warmup, ws, clocks=None):
-    """Device-timed propagation of `steps` RK4 steps (inputs resident in HBM)."""
+def time_gpu(prop, precision, steps, warmup, ws, clocks=None, schedule=None):
+    """Device-timed propagation of `steps` RK4 steps (inputs resident in HBM).  schedule: (occupancy %,
+    chunks per warp) forced on the body launches instead of the tuner's choice."""
     import torch
 
     from paper_1803_03498_gb300 import heom
 
     run = heom.Run(prop.system, prop.rho0_re, prop.rho0_im, precision=precision, w=prop.w,
                    max_records=warmup + steps + 4)
+    if schedule is not None:
+        run.set_schedule(*schedule, part=0)
     run.propagate(prop.dt_fs, warmup, 1)
     torch.cuda.synchronize()
     run.set_timing(True)
@@ -415,8 +418,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 variant (0: steps/20)")
     ap.add_argument("--depth", type=int, default=0, help="override the hierarchy depth (profiling cases)")
     ap.add_argument("--tc-steps", type=int, default=0, help="timed steps of the split-TF32 variant (0: steps/10)")
-    ap.add_argument("--only", default="", choices=["", "mixed", "fp64", "split_tf32"],
-                    help="time one precision only, no end-to-end or CPU legs (profiling cases)")
+    ap.add_argument("--only", default="", choices=["", "mixed", "fp64", "split_tf32", "dipole", "field"],
+                    help="one case only, no end-to-end or CPU legs, no autotuning (profiling cases): a precision "
+                         "of the LHCII-like population run, its linear-absorption run (dipole: 15 states, column-0 "
+                         "layout, mixed), or the pumped two-exciton leg (field)")
+    ap.add_argument("--schedule", default="", help="profiling cases: occupancy%%,chunks_per_warp of the body launches")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -445,10 +451,21 @@ def main():
         prop.system.name = prop.system.name.replace("D=6", f"D={args.depth}")
     n_ado = prop.system.n_ado
     if args.only:
-        prec = {"mixed": "fp32_mixed", "fp64": "fp64", "split_tf32": "split_tf32"}[args.only]
-        ms, launches, kt, obs, _ = time_gpu(prop, prec, args.steps, args.warmup, ws, None)
+        heom.set_autotune(0)  # the same launches every time: no tuning probes before the captured ones
+        if args.only == "field":
+            if rank == 0:
+                print(json.dumps({"profile_case": "two_exciton_field", **time_field(steps=args.steps,
+                                                                                   warmup=args.warmup)}), flush=True)
+            return 0
+        sched = tuple(int(x) for x in args.schedule.split(",")) if args.schedule else None
+        prec = {"mixed": "fp32_mixed", "fp64": "fp64", "split_tf32": "split_tf32", "dipole": "fp32_mixed"}[args.only]
+        case = prop
+        if args.only == "dipole":  # seeded unit dipoles, e_p = x
+            dip = wl.unit_dipoles(np.random.default_rng(1803013), prop.system.N)
+            case = wl.dipole_runs(prop.system, dip, prop.dt_fs, args.steps, "lhcii")[0]
+        ms, launches, kt, obs, _ = time_gpu(case, prec, args.steps, args.warmup, ws, None, schedule=sched)
         if rank == 0:
-            print(json.dumps({"profile_case": prop.system.name, "precision": prec, "n_ado": n_ado,
+            print(json.dumps({"profile_case": case.system.name, "precision": prec, "n_ado": n_ado,
                               "ms_per_step": ms / args.steps, "kernel": kt, "launches": launches}), flush=True)
         return 0
     clocks = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
