@@ -14,10 +14,11 @@
 // warp shuffles.  A warp works on G consecutive chunks at once (G, the chunks per warp, is a
 // launch-schedule choice of the autotuner; at most 32 ADOs per warp step): each lane holds one
 // element of each, and the link records of all of them load together, G per lane per window of 32 G,
-// followed by the neighbour elements they name.  The products reach their owning lanes by warp
-// shuffles in record order.  Every G sums the same terms in the same order for each element, and
-// the serial memory round trips of a warp step (offsets, records, neighbour elements) are shared
-// by G chunks.
+// followed by the neighbour elements they name.  The products reach their owning lanes through a
+// per-warp shared-memory list read in record order (one broadcast load per record), and H x reads
+// the chunk's column from shared memory (one broadcast load per term).  Every G sums the same terms
+// in the same order for each element, and the serial memory round trips of a warp step (offsets,
+// records, neighbour elements) are shared by G chunks.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -62,9 +63,23 @@ __device__ __forceinline__ typename VCplx<CT>::type vec_load(const StateView &s,
 // FP64 head kernel of a mixed-precision run (its own ADOs are in the head region); otherwise the
 // own ADOs are in the body region of storage type BT == CT.  hrow: row li of H; h00 = H_00;
 // term_i = Delta of state li.
+// A link product on its way to its owner lane (per-warp shared-memory list).
+template <typename CT>
+struct alignas(16) VecDel {
+  CT cr, ci;
+  int owner;
+};
+
+// Shared memory of one warp: the delivery list of a window and the columns of its chunks.
+template <typename CT, int GE>
+struct VecWarpSmem {
+  VecDel<CT> del[32 * GE];
+  typename VCplx<CT>::type xs[32 * GE];
+};
+
 template <int N, typename CT, typename BT, int G>
 __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[N], CT h00, CT term_i, CT ch,
-                                         int step, int lane) {
+                                         int step, int lane, VecWarpSmem<CT, vec_group(N, G)> &ws) {
   using C2 = typename VCplx<CT>::type;
   constexpr int A = 32 / N;
   constexpr int GE = vec_group(N, G);
@@ -90,17 +105,22 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
       if (has_y) yv[g] = vec_load<N, CT, BT>(c.y, c.u_split, u0 + a, li);
     }
   }
-  // -i (H x)_i + i H_00 x_i, then decay and terminator
+  // -i (H x)_i + i H_00 x_i, then decay and terminator; the columns go through shared memory (every
+  // lane of an ADO reads the same word: one broadcast load per term)
+  __syncwarp();  // the previous step's readers of ws are done
+#pragma unroll
+  for (int g = 0; g < GE; ++g) ws.xs[g * 32 + lane] = x[g];
+  __syncwarp();
 #pragma unroll
   for (int g = 0; g < GE; ++g) {
     rr[g] = -h00 * x[g].y;
     ri[g] = h00 * x[g].x;
+    const C2 *col = ws.xs + g * 32 + min(la, A - 1) * N;
 #pragma unroll
     for (int b = 0; b < N; ++b) {
-      const CT xr = __shfl_sync(0xffffffffu, x[g].x, min(la, A - 1) * N + b);
-      const CT xi = __shfl_sync(0xffffffffu, x[g].y, min(la, A - 1) * N + b);
-      rr[g] = fma(hrow[b], xi, rr[g]);
-      ri[g] = fma(-hrow[b], xr, ri[g]);
+      const C2 xb = col[b];
+      rr[g] = fma(hrow[b], xb.y, rr[g]);
+      ri[g] = fma(-hrow[b], xb.x, ri[g]);
     }
     const int a = g * A + la;
     if (lane_ok && a < cnt) {
@@ -111,8 +131,8 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
   }
   // links, 32 GE records of the step at a time: lane l loads records base + 32 q + l (q < GE), then
   // the neighbour element s each names, and forms R v_s; the contributions then go to their owner
-  // (chunk g, lane (a, s)), o = g A + a the record's ADO in the step (tag u mod 32), by a uniform
-  // shuffle loop over the records in order
+  // (chunk g, lane (a, s)), o = g A + a the record's ADO in the step (tag u mod 32), through the
+  // warp's delivery list, read by every lane in record order
   {
     const int64_t lo = c.link_off[u0], hi = c.link_off[u0 + cnt];
     for (int64_t base = lo; base < hi; base += 32 * GE) {
@@ -140,22 +160,26 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
           ci[q] = fma(rq[q].re, v.y, rq[q].im * v.x);
         }
       }
+      __syncwarp();  // the previous window's readers of the list are done
 #pragma unroll
       for (int q = 0; q < GE; ++q) {
-        const int64_t b0 = base + q * 32;
-        if (b0 >= hi) break;  // uniform across the warp
-        const int w = (int)min((int64_t)32, hi - b0);
-        for (int k = 0; k < w; ++k) {
-          const int o = __shfl_sync(0xffffffffu, owner[q], k);
-          const CT pr = __shfl_sync(0xffffffffu, cr[q], k);
-          const CT pi = __shfl_sync(0xffffffffu, ci[q], k);
+        VecDel<CT> d;
+        d.cr = cr[q];
+        d.ci = ci[q];
+        d.owner = owner[q];
+        ws.del[q * 32 + lane] = d;
+      }
+      __syncwarp();
+      const int w = (int)min((int64_t)32 * GE, hi - base);
+#pragma unroll 4
+      for (int k = 0; k < w; ++k) {
+        const VecDel<CT> d = ws.del[k];
 #pragma unroll
-          for (int g = 0; g < GE; ++g)
-            if (o == g * 32 + lane) {
-              rr[g] += pr;
-              ri[g] += pi;
-            }
-        }
+        for (int g = 0; g < GE; ++g)
+          if (d.owner == g * 32 + lane) {
+            rr[g] += d.cr;
+            ri[g] += d.ci;
+          }
       }
     }
   }
@@ -194,7 +218,9 @@ __global__ void __launch_bounds__(kVecWarps * 32) vec_stage_kernel(const __grid_
   const CT h00 = a.H[0];
   const CT term_i = lane_ok ? a.term[li] : (CT)0;
   const int n_steps = (c.u_end - c.u_begin + SA - 1) / SA;
-  for (int sp = gw; sp < n_steps; sp += nw) vec_step<N, CT, BT, G>(c, hrow, h00, term_i, a.ch, sp, lane);
+  __shared__ VecWarpSmem<CT, vec_group(N, G)> wsm[kVecWarps];
+  VecWarpSmem<CT, vec_group(N, G)> &ws = wsm[threadIdx.x >> 5];
+  for (int sp = gw; sp < n_steps; sp += nw) vec_step<N, CT, BT, G>(c, hrow, h00, term_i, a.ch, sp, lane, ws);
 }
 
 // Many runs of the same N in one launch (ragged batches): run k's warp steps (of vec_group(N, G)
@@ -209,6 +235,8 @@ __global__ void __launch_bounds__(kVecWarps * 32) vec_batch_kernel(const __grid_
   const int la = lane / N, li = lane - la * N;
   const bool lane_ok = la < A;
   const int64_t total = a.chunk0[a.nruns];
+  __shared__ VecWarpSmem<CT, vec_group(N, G)> wsm[kVecWarps];
+  VecWarpSmem<CT, vec_group(N, G)> &ws = wsm[threadIdx.x >> 5];
   int k = 0;
   for (int64_t g = gw; g < total; g += nw) {
     int lo = 0, hi = a.nruns - 1;  // the run holding global chunk g
@@ -224,7 +252,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) vec_batch_kernel(const __grid_
 #pragma unroll
     for (int b = 0; b < N; ++b) hrow[b] = lane_ok ? (CT)__ldg(&d->H[li * kMaxStates + b]) : (CT)0;
     const CT h00 = (CT)__ldg(&d->H[0]), term_i = lane_ok ? (CT)__ldg(&d->term[li]) : (CT)0;
-    vec_step<N, CT, BT, G>(c, hrow, h00, term_i, (CT)__ldg(&d->ch), (int)(g - a.chunk0[k]), lane);
+    vec_step<N, CT, BT, G>(c, hrow, h00, term_i, (CT)__ldg(&d->ch), (int)(g - a.chunk0[k]), lane, ws);
   }
   (void)k;
 }
