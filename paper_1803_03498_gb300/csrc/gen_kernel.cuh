@@ -14,7 +14,10 @@
 // and per link record (v, s, R): R v_sj added to element (s, j) and conj(R) v_is to element (i, s)
 // (both for i = j = s: 2 Re R on the diagonal), as for every other kernel.
 //
-// One warp per ADO: lane j owns column j (N <= 32).  The input tile is staged in shared memory
+// A warp works on rows [i0, i1) of one ADO -- all rows, or a share of them when a launch has fewer
+// ADOs than SMs (the FP64 head of a mixed run): element (i, j) needs only row i's own terms, so the
+// rows of an ADO can go to warps on different SMs (GB300's FP64 pipe, 2 FMA per clock per SM, is
+// then shared by fewer warps).  Lane j owns column j (N <= 32).  The input tile is staged in shared memory
 // (column reads conflict-free, row reads broadcast); H, Im H and T sit in shared memory once per
 // CTA.  The commutator, decay and terminator go to a result tile R that lane j writes in column j;
 // the row parts of the links also land in column j of R (lane j loads v_sj, coalesced), the column
@@ -76,12 +79,16 @@ __device__ __forceinline__ void gen_store(const StateView &s, int E, int Ep, int
 
 // Kind as the other kernels: (double, double) FP64; (float, float) mixed body; (double, float) mixed
 // head (own ADOs in the FP64 head region, neighbours in either region).
-template <typename CT, typename BT>
-__global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_constant__ GenArgs<CT> a) {
+// kSplit: the launch splits ADO rows over warps (splits > 1); otherwise every warp takes whole ADOs.
+template <typename CT, typename BT, bool kSplit>
+__global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_constant__ GenArgs<CT> a, int splits_arg) {
   using C2 = typename GCplx<CT>::type;
   constexpr bool kOwnHead = sizeof(CT) == 8 && sizeof(BT) == 4;
   const StageCommon &c = a.c;
   const int N = c.n, E = c.E, Ep = c.Ep;
+  const int splits = kSplit ? splits_arg : 1;
+  const int wpc = blockDim.x >> 5;             // warps per CTA
+  const int rows = kSplit ? (N + splits - 1) / splits : N;  // rows per task
   extern __shared__ __align__(16) unsigned char gsm[];
   CT *Hs = reinterpret_cast<CT *>(gsm);  // [N][N] Re H(t), then Im H(t), then T
   CT *His = Hs + E;
@@ -104,13 +111,16 @@ __global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_
   const bool has_b2 = a.base2.head != nullptr || a.base2.body != nullptr;
   const int j = lane;
   const bool lj = j < N;
-  const int gw = blockIdx.x * kGenWarps + warp, nw = gridDim.x * kGenWarps;
-  for (int64_t u = c.u_begin + gw; u < c.u_end; u += nw) {
+  const int64_t gw = (int64_t)blockIdx.x * wpc + warp, nw = (int64_t)gridDim.x * wpc;
+  const int64_t n_tasks = (int64_t)(c.u_end - c.u_begin) * splits;
+  for (int64_t task = gw; task < n_tasks; task += nw) {
+    const int64_t u = c.u_begin + (kSplit ? task / splits : task);
+    const int i0 = kSplit ? (int)(task % splits) * rows : 0, i1 = kSplit ? min(N, i0 + rows) : N;
     for (int e = lane; e < E; e += 32) Z[e] = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, u, e);
     __syncwarp();
     const CT g = (CT)c.gsum[u];
     if (lj) {
-      for (int i = 0; i < N; ++i) {
+      for (int i = i0; i < i1; ++i) {
         // -i (H s - s H)_ij with H = Hr + i Hi
         CT pr = 0, pi = 0;  // (H s - s H)_ij
         for (int k = 0; k < N; ++k) {
@@ -142,14 +152,14 @@ __global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_
         const int v = __shfl_sync(0xffffffffu, mine.v, k);
         const int s = __shfl_sync(0xffffffffu, mine.s, k) & kRecStateMask;
         const CT rre = __shfl_sync(0xffffffffu, mine.re, k), rim = __shfl_sync(0xffffffffu, mine.im, k);
-        if (lj) {
-          // row part: element (s, j) += R v_sj (lane j, column j of R)
+        if (lj && s >= i0 && s < i1) {  // row part: element (s, j) += R v_sj (lane j, column j of R)
           const C2 vs = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, v, s * N + j);
-          // column part: element (i = j, s) += conj(R) v_js (lane j, row j of Z)
-          const C2 vc = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, v, j * N + s);
           C2 &rs = R[s * N + j];
           rs.x += rre * vs.x - rim * vs.y;
           rs.y += rre * vs.y + rim * vs.x;
+        }
+        if (j >= i0 && j < i1) {  // column part: element (i = j, s) += conj(R) v_js (lane j, row j of Z)
+          const C2 vc = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, v, j * N + s);
           C2 &zc = Z[j * N + s];
           zc.x += rre * vc.x + rim * vc.y;
           zc.y += rre * vc.y - rim * vc.x;
@@ -158,7 +168,7 @@ __global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_
     }
     __syncwarp();
     if (lj) {
-      for (int i = 0; i < N; ++i) {
+      for (int i = i0; i < i1; ++i) {
         const int e = i * N + j;
         const C2 r = R[e], z = Z[e];
         const CT kr = r.x + z.x, ki = r.y + z.y;
@@ -184,30 +194,45 @@ template <typename CT, typename BT>
 int launch_gen_kind(const GenArgs<CT> &a, cudaStream_t st, int sm_count) {
   const StageCommon &c = a.c;
   if (c.u_end <= c.u_begin) return 0;
-  const size_t smem = ((((size_t)3 * c.E * sizeof(CT)) + 15) & ~(size_t)15) +
-                      (size_t)kGenWarps * 2 * c.E * sizeof(typename GCplx<CT>::type);
+  const int64_t n = c.u_end - c.u_begin;
+  // fewer ADOs than SMs: split each ADO's rows over single-warp CTAs on different SMs
+  const int splits = n * 2 <= sm_count ? (int)std::min<int64_t>(c.n, (sm_count + n - 1) / n) : 1;
+  const int wpc = splits > 1 ? 1 : kGenWarps;
+  const size_t head_bytes = (((size_t)3 * c.E * sizeof(CT)) + 15) & ~(size_t)15;
+  const size_t smem = head_bytes + (size_t)wpc * 2 * c.E * sizeof(typename GCplx<CT>::type);
   const size_t smem_max = ((((size_t)3 * kGenMaxStates * kGenMaxStates * sizeof(CT)) + 15) & ~(size_t)15) +
                           (size_t)kGenWarps * 2 * kGenMaxStates * kGenMaxStates * sizeof(typename GCplx<CT>::type);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gen_stage_kernel<CT, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(gen_stage_kernel<CT, BT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_max);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gen_stage_kernel<CT, BT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_max);
     if (e != cudaSuccess) {
       set_error(std::string("general stage kernel: shared memory attribute: ") + cudaGetErrorString(e));
       return -4;
     }
     attr = true;
   }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gen_stage_kernel<CT, BT>, kGenWarps * 32, smem);
-  if (e != cudaSuccess || per_sm < 1) {
-    set_error(std::string("general stage kernel: occupancy query failed: ") + cudaGetErrorString(e));
-    return -4;
+  static int occ[2][kGenMaxStates + 1] = {{0}};  // CTAs per SM by CTA shape and n_states
+  int &per_sm = occ[wpc == 1 ? 0 : 1][c.n];
+  cudaError_t e;
+  if (per_sm == 0) {
+    int ps = 0;
+    e = splits > 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, gen_stage_kernel<CT, BT, true>, wpc * 32, smem)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, gen_stage_kernel<CT, BT, false>, wpc * 32, smem);
+    if (e != cudaSuccess || ps < 1) {
+      set_error(std::string("general stage kernel: occupancy query failed: ") + cudaGetErrorString(e));
+      return -4;
+    }
+    per_sm = ps;
   }
-  const int64_t n = c.u_end - c.u_begin;
+  const int64_t tasks = n * splits;
   const int grid = (int)std::max<int64_t>(
-      1, std::min<int64_t>((n + kGenWarps - 1) / kGenWarps, (int64_t)sched_ctas(per_sm, c.occ_pct) * sm_count));
-  gen_stage_kernel<CT, BT><<<grid, kGenWarps * 32, smem, st>>>(a);
+      1, std::min<int64_t>((tasks + wpc - 1) / wpc, (int64_t)sched_ctas(per_sm, c.occ_pct) * sm_count));
+  if (splits > 1) gen_stage_kernel<CT, BT, true><<<grid, wpc * 32, smem, st>>>(a, splits);
+  else gen_stage_kernel<CT, BT, false><<<grid, wpc * 32, smem, st>>>(a, 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("general stage kernel launch: ") + cudaGetErrorString(e));
