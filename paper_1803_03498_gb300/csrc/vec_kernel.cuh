@@ -14,9 +14,10 @@
 // warp shuffles.  A warp works on G consecutive chunks at once (G, the chunks per warp, is a
 // launch-schedule choice of the autotuner; at most 32 ADOs per warp step): each lane holds one
 // element of each, and the link records of all of them load together, G per lane per window of 32 G,
-// followed by the neighbour elements they name.  The products reach their owning lanes through a
-// per-warp shared-memory list read in record order (one broadcast load per record), and H x reads
-// the chunk's column from shared memory (one broadcast load per term).  Every G sums the same terms
+// followed by the neighbour elements they name.  The products go into a per-warp shared-memory list
+// in record order; records are sorted by ADO and state, so each owner's products form one segment,
+// whose bounds a per-window table gives to the owner lane, which adds them in order.  H x reads the
+// chunk's column from shared memory (one broadcast load per term).  Every G sums the same terms
 // in the same order for each element, and the serial memory round trips of a warp step (offsets,
 // records, neighbour elements) are shared by G chunks.
 #pragma once
@@ -63,17 +64,12 @@ __device__ __forceinline__ typename VCplx<CT>::type vec_load(const StateView &s,
 // FP64 head kernel of a mixed-precision run (its own ADOs are in the head region); otherwise the
 // own ADOs are in the body region of storage type BT == CT.  hrow: row li of H; h00 = H_00;
 // term_i = Delta of state li.
-// A link product on its way to its owner lane (per-warp shared-memory list).
-template <typename CT>
-struct alignas(16) VecDel {
-  CT cr, ci;
-  int owner;
-};
-
-// Shared memory of one warp: the delivery list of a window and the columns of its chunks.
+// Shared memory of one warp: the link products of a window in record order, the segment of each
+// owner in it, and the columns of the step's chunks.
 template <typename CT, int GE>
 struct VecWarpSmem {
-  VecDel<CT> del[32 * GE];
+  typename VCplx<CT>::type del[32 * GE];  // R v of window entry k
+  int first[32 * GE], end[32 * GE];       // per owner (g 32 + lane): its entries [first, end)
   typename VCplx<CT>::type xs[32 * GE];
 };
 
@@ -131,8 +127,9 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
   }
   // links, 32 GE records of the step at a time: lane l loads records base + 32 q + l (q < GE), then
   // the neighbour element s each names, and forms R v_s; the contributions then go to their owner
-  // (chunk g, lane (a, s)), o = g A + a the record's ADO in the step (tag u mod 32), through the
-  // warp's delivery list, read by every lane in record order
+  // (chunk g, lane (a, s)), o = g A + a the record's ADO in the step (tag u mod 32): entry k of the
+  // window's list holds record base + k, the owner's entries are contiguous (records sorted by ADO
+  // and state), and the owner adds its segment in order
   {
     const int64_t lo = c.link_off[u0], hi = c.link_off[u0 + cnt];
     for (int64_t base = lo; base < hi; base += 32 * GE) {
@@ -160,26 +157,42 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
           ci[q] = fma(rq[q].re, v.y, rq[q].im * v.x);
         }
       }
-      __syncwarp();  // the previous window's readers of the list are done
+      __syncwarp();  // the previous window's readers of the list and the table are done
 #pragma unroll
       for (int q = 0; q < GE; ++q) {
-        VecDel<CT> d;
-        d.cr = cr[q];
-        d.ci = ci[q];
-        d.owner = owner[q];
+        C2 d;
+        d.x = cr[q];
+        d.y = ci[q];
         ws.del[q * 32 + lane] = d;
+        ws.first[q * 32 + lane] = 0;
+        ws.end[q * 32 + lane] = 0;
       }
       __syncwarp();
-      const int w = (int)min((int64_t)32 * GE, hi - base);
-#pragma unroll 4
-      for (int k = 0; k < w; ++k) {
-        const VecDel<CT> d = ws.del[k];
+      // segment bounds: entry k starts its owner's segment when entry k - 1 has another owner, and
+      // ends it when entry k + 1 has another owner (invalid entries have owner -1)
 #pragma unroll
-        for (int g = 0; g < GE; ++g)
-          if (d.owner == g * 32 + lane) {
-            rr[g] += d.cr;
-            ri[g] += d.ci;
-          }
+      for (int q = 0; q < GE; ++q) {
+        const int up = __shfl_up_sync(0xffffffffu, owner[q], 1);
+        const int dn = __shfl_down_sync(0xffffffffu, owner[q], 1);
+        const int pq = __shfl_sync(0xffffffffu, owner[q > 0 ? q - 1 : 0], 31);
+        const int nq = __shfl_sync(0xffffffffu, owner[q + 1 < GE ? q + 1 : q], 0);
+        const int prev = lane > 0 ? up : (q > 0 ? pq : -2);
+        const int next = lane < 31 ? dn : (q + 1 < GE ? nq : -2);
+        const int o = owner[q], k = q * 32 + lane;
+        if (o >= 0) {
+          if (o != prev) ws.first[o] = k;
+          if (o != next) ws.end[o] = k + 1;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int g = 0; g < GE; ++g) {
+        const int f = ws.first[g * 32 + lane], e = ws.end[g * 32 + lane];
+        for (int k = f; k < e; ++k) {
+          const C2 d = ws.del[k];
+          rr[g] += d.x;
+          ri[g] += d.y;
+        }
       }
     }
   }
