@@ -10,8 +10,8 @@
 //               + sum over the links of u through a mode of state a of R v_a
 // with the link coefficients R of the full form (its column part and diagonal part vanish here).
 // out_u = y_u + ch (L zin)_u as in stage_kernel (Horner RK4).  A chunk is A = floor(32 / N)
-// consecutive ADOs; lane (a, i) of a warp holds element i of ADO a of a chunk, and H x goes through
-// warp shuffles.  A warp works on G consecutive chunks at once (G, the chunks per warp, is a
+// consecutive ADOs; lane (a, i) of a warp holds element i of ADO a of a chunk.  A warp works on G
+// consecutive chunks at once (G, the chunks per warp, is a
 // launch-schedule choice of the autotuner; at most 32 ADOs per warp step): each lane holds one
 // element of each, and the link records of all of them load together, G per lane per window of 32 G,
 // followed by the neighbour elements they name.  The products go into a per-warp shared-memory list
