@@ -51,7 +51,7 @@ def _traffic():
 
     src = os.path.join(ROOT, "paper_1803_03498_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("stage_kernel.cuh", "heom_abi.cu"):
+    for f in ("stage_kernel.cuh", "propagate.cu"):  # the kernel and the driver that launches it
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
     vals = {}
