@@ -122,12 +122,20 @@ __global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_
     if (lj) {
       for (int i = i0; i < i1; ++i) {
         // -i (H s - s H)_ij with H = Hr + i Hi
-        CT pr = 0, pi = 0;  // (H s - s H)_ij
+        // (H s - s H)_ij as a chain of FMAs, four per component and k (on GB300 every FP64 warp
+        // instruction occupies the SM's FP64 pipe for 16 cycles: no separate multiplies and adds)
+        CT pr = 0, pi = 0;
         for (int k = 0; k < N; ++k) {
           const C2 skj = Z[k * N + j], sik = Z[i * N + k];
           const CT hr1 = Hs[i * N + k], hi1 = His[i * N + k], hr2 = Hs[k * N + j], hi2 = His[k * N + j];
-          pr += hr1 * skj.x - hi1 * skj.y - (sik.x * hr2 - sik.y * hi2);
-          pi += hr1 * skj.y + hi1 * skj.x - (sik.x * hi2 + sik.y * hr2);
+          pr = fma(hr1, skj.x, pr);
+          pr = fma(-hi1, skj.y, pr);
+          pr = fma(-sik.x, hr2, pr);
+          pr = fma(sik.y, hi2, pr);
+          pi = fma(hr1, skj.y, pi);
+          pi = fma(hi1, skj.x, pi);
+          pi = fma(-sik.x, hi2, pi);
+          pi = fma(-sik.y, hr2, pi);
         }
         const C2 sij = Z[i * N + j];
         const CT f = g + Ts[i * N + j];
