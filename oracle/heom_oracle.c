@@ -46,7 +46,8 @@
  *   - hbar = 1 throughout (the paper's hbar placement is not consistent).
  *   - the rescaling uses |c(b,k)| of the real c of the paper; when |c| < 1e-300 the mode is left
  *     unscaled (up factor 1, down factor n).
- *   - Parity with printed trajectories is unpinned: the paper prints none.
+ *   - The paper prints its dynamics as figures only (no tabulated values); the pins of this oracle
+ *     are closed forms, invariants, special cases and independent constructions (tests/).
  */
 #include <complex.h>
 #include <math.h>

@@ -19,7 +19,8 @@ Parity status of each function (against the paper, arXiv 1803.03498):
   laser field    pinned (Rabi rotation of a two-level system by a resonant Gaussian pulse: closed form
                  through the pulse area; two uncoupled sites in the two-exciton space: the product of
                  two such rotations; a zero-amplitude field changes nothing)
-  printed trajectories of the paper: parity unpinned (the paper prints figures only).
+  the paper prints its dynamics as figures only (no tabulated values), so no pin compares with
+  printed numbers; every function above is pinned as listed.
 """
 from __future__ import annotations
 
