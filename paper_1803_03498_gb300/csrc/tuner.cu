@@ -21,9 +21,9 @@ using namespace heom;
 
 namespace heom {
 std::atomic<int> g_autotune{3};  // timed launches per candidate at creation (0: off)
-std::mutex g_tune_mu;                                    // guards the cache
-std::map<std::array<int, 7>, heom_schedule> g_tune_cache;  // (layout, precision, part, n, herm, cplx, log2 ADOs)
-heom_schedule g_default[3] = {{100, 1}, {100, 1}, {100, 1}};  // per layout, without cache entry or tuning
+static std::mutex g_tune_mu;  // guards the cache and the defaults
+static std::map<std::array<int, 7>, heom_schedule> g_tune_cache;  // (layout, precision, part, n, herm, cplx, log2 ADOs)
+static heom_schedule g_default[3] = {{100, 1}, {100, 1}, {100, 1}};  // per layout, without cache entry or tuning
 
 heom_schedule default_for(int layout) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -50,12 +50,12 @@ std::vector<heom_schedule> candidates(int layout) {
   return v;  // the default {100, 1} first: ties keep it
 }
 
-bool valid_schedule(const heom_schedule &s) {
+static bool valid_schedule(const heom_schedule &s) {
   return s.occupancy_pct >= 1 && s.occupancy_pct <= 100 &&
          (s.chunks_per_warp == 1 || s.chunks_per_warp == 2 || s.chunks_per_warp == 4);
 }
 
-std::array<int, 7> run_key(const heom_run *r, int part) {
+static std::array<int, 7> run_key(const heom_run *r, int part) {
   const int64_t cnt = part == 1 ? r->u_split : r->n_ado - (r->precision == HEOM_FP64 ? 0 : r->u_split);
   return {r->vec ? 1 : 0, r->precision, part, r->n, r->herm ? 1 : 0, r->cplx_h ? 1 : 0, ilog2(cnt)};
 }
@@ -73,13 +73,13 @@ void cache_put(const std::array<int, 7> &k, const heom_schedule &s) {
   g_tune_cache[k] = s;
 }
 
-bool capturing(cudaStream_t s) {
+static bool capturing(cudaStream_t s) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
 }
 
 
-int tune_part(heom_run *r, int part, int reps, std::vector<heom_schedule> &tried, std::vector<double> &ms) {
+static int tune_part(heom_run *r, int part, int reps, std::vector<heom_schedule> &tried, std::vector<double> &ms) {
   if (capturing(r->stream)) {
     set_error("heom_tune: the run's stream is being captured");
     return HEOM_E_STATE;
