@@ -142,3 +142,13 @@ def test_general_runs_bytes_and_mask_checks(lib):
     g7, _ = wl.fmo_two_exciton(n_sites=7, D=1)
     assert g7.system.N == 29
     heom.run_bytes(g7.system, heom.Hierarchy(g7.system.n_modes, 1), "fp32_mixed", 1)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libheom.so the binding raises instead of computing anything."""
+    monkeypatch.setattr(heom, "_lib", None)
+    monkeypatch.setattr(heom, "LIB_PATH", str(tmp_path / "libheom.so"))
+    with pytest.raises(RuntimeError, match="libheom.so not found"):
+        heom.load()
+    with pytest.raises(RuntimeError):
+        heom.Hierarchy(2, 2)
