@@ -207,9 +207,11 @@ typedef struct {
 } heom_field;
 int heom_run_set_field(heom_run *r, const heom_field *f);
 
-/* Length in doubles of one observable record: n_states populations Re sigma_0[a][a], then
- * Re Tr sigma_0, Im Tr sigma_0, Re C, Im C (C = sum_a w_a sigma_0[a][0], 0 without dip_w), then
- * max_ij |sigma_0[i][j] - conj(sigma_0[j][i])|.  That is n_states + 5. */
+/* Length in doubles of one observable record of the reduced density matrix rho = sigma_0 (the root
+ * ADO, section "HEOM formalism"): n_states populations Re sigma_0[a][a], then Re Tr sigma_0,
+ * Im Tr sigma_0, Re C, Im C (C = sum_a w_a sigma_0[a][0], the dipole correlation of Eq.
+ * lin_abs_mukamel; 0 without dip_w), then max_ij |sigma_0[i][j] - conj(sigma_0[j][i])|.  That is
+ * n_states + 5; 0 for a NULL run. */
 int heom_record_len(const heom_run *r);
 
 /*
@@ -220,7 +222,8 @@ int heom_record_len(const heom_run *r);
  */
 int heom_observables(heom_run *r, double *out, int64_t cap_records, int64_t *written);
 
-/* Synchronises; copies sigma_0 (FP64) into caller host arrays of n_states^2 doubles. */
+/* Synchronises; copies the reduced density matrix rho = sigma_0 (the root ADO, section "HEOM
+ * formalism"; FP64 in every precision) into caller host arrays of n_states^2 doubles, row-major. */
 int heom_get_sigma0(heom_run *r, double *re, double *im);
 
 /* Synchronises; copies ADOs [u0, u0 + count) of the current state into / out of caller host
@@ -355,11 +358,10 @@ int heom_batch_schedule(const heom_batch *b, int g, int part, heom_schedule *out
 
 /*
  * heom_propagate_static -- one complete propagation that allocates no device memory, for callers
- * that cannot call cudaMalloc (code running while its stream is being captured into a CUDA graph,
- * plug-ins whose host application owns every device allocation, latency-critical paths that cannot
- * afford the implicit synchronisation of cudaMalloc/cudaFree).  The paper has no counterpart; it
- * is a deployment convenience around the same kernels as heom_run_create + heom_propagate +
- * heom_observables.
+ * that cannot call cudaMalloc (plug-ins whose host application owns every device allocation and
+ * hands the library no buffer, latency-critical paths that cannot afford the implicit
+ * synchronisation of cudaMalloc/cudaFree).  The paper has no counterpart; it is a deployment
+ * convenience around the same kernels as heom_run_create + heom_propagate + heom_observables.
  *   Inputs (host, read during the call): sys, h, precision, sigma0_re/sigma0_im (n_states^2,
  *   sigma0_im may be NULL), dip_w (n_states or NULL), dt_fs, n_steps, obs_stride, as for
  *   heom_run_create and heom_propagate; cuda_stream as there.
@@ -370,12 +372,13 @@ int heom_batch_schedule(const heom_batch *b, int g, int part, heom_schedule *out
  * lives in one library-owned static device array of 32 MiB (33554432 bytes) per GPU, which every GPU
  * that loads the library holds until the process exits.  A run whose heom_run_bytes exceeds it is
  * rejected with HEOM_E_NOMEM before any work.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  Every call reuses the same array and zeroes what must start at zero; calls
- * serialise on a lock within one process, and calls whose GPU work overlaps (for example from two
- * processes sharing a context, or work still in flight on another stream) would race on it.  The
- * call synchronises the stream before it returns.  Errors: those of heom_run_bytes,
- * heom_run_create, heom_propagate and heom_observables, and HEOM_E_NOMEM as above.
+ * device address (cudaGetSymbolAddress) with that device current.  Every call reuses the same array
+ * and zeroes what must start at zero; calls serialise on a lock within one process, and calls whose
+ * GPU work overlaps (for example from two processes sharing a context, or work still in flight on
+ * another stream) would race on it.  On every return path, errors included, the call has waited
+ * for the work it queued (on the stream and on the run's side stream) before it returns.  Errors:
+ * those of heom_run_bytes, heom_run_create, heom_propagate and heom_observables, and HEOM_E_NOMEM
+ * as above.
  */
 int heom_propagate_static(const heom_system *sys, const heom_hier *h, int precision, const double *sigma0_re,
                           const double *sigma0_im, const double *dip_w, double dt_fs, int64_t n_steps,

@@ -229,14 +229,12 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
         for (int i : b->gruns[g]) {
           heom_run *r = b->runs[i];
           cudaStream_t own = r->stream;
-          const int64_t l0 = r->launches, rec0 = r->records_host, max0 = r->max_records;
+          const int64_t l0 = r->launches, rec0 = r->records_host;
           r->stream = b->gstream[g];
-          r->max_records = INT64_MAX;
-          rc = enqueue_record(r);
+          rc = enqueue_record(r, false);  // counts are checked per replay by heom_batch_launch
           b->launches_per_replay[i] += r->launches - l0;
           r->launches = l0;
           r->records_host = rec0;  // advanced by heom_batch_launch
-          r->max_records = max0;
           r->stream = own;
           if (rc != HEOM_OK) break;
         }
@@ -247,20 +245,18 @@ extern "C" int heom_batch_create(heom_run *const *runs, int n_runs, double dt_fs
     if (grouped[i]) continue;
     heom_run *r = b->runs[i];
     cudaStream_t own = r->stream;
-    const int64_t l0 = r->launches, rec0 = r->records_host, max0 = r->max_records;
-    r->stream = b->pool[i % P];
-    r->max_records = INT64_MAX;  // counters are restored below; launches advance them
+    const int64_t l0 = r->launches, rec0 = r->records_host;
+    r->stream = b->pool[i % P];  // counters are restored below; launches advance them
     for (int64_t s = 0; s < steps_per_launch && rc == HEOM_OK; ++s) {
       if ((rc = run_stage(r, r->y, r->y, r->zA, h / 4))) break;
       if ((rc = run_stage(r, r->zA, r->y, r->zB, h / 3))) break;
       if ((rc = run_stage(r, r->zB, r->y, r->zA, h / 2))) break;
       if ((rc = run_stage(r, r->zA, r->y, r->y, h))) break;
-      if (obs_stride > 0 && (s + 1) % obs_stride == 0) rc = enqueue_record(r);
+      if (obs_stride > 0 && (s + 1) % obs_stride == 0) rc = enqueue_record(r, false);
     }
     b->launches_per_replay[i] = r->launches - l0;
     r->launches = l0;
     r->records_host = rec0;
-    r->max_records = max0;
     r->stream = own;
   }
   for (int p = 0; p < P && e == cudaSuccess; ++p) {

@@ -408,8 +408,8 @@ static StateView view_at(char *base, const Layout &L, int c) {
   return v;
 }
 
-int heom::enqueue_record(heom_run *r) {
-  if (r->records_host >= r->max_records) {
+int heom::enqueue_record(heom_run *r, bool host_check) {
+  if (host_check && r->records_host >= r->max_records) {
     set_error("observable record buffer full (max_records)");
     return HEOM_E_NOMEM;
   }

@@ -97,7 +97,10 @@ struct heom_run {
 namespace heom {
 
 // run set-up and state I/O (heom_abi.cu)
-int enqueue_record(heom_run *r);  // one observable record of sigma_0 on the run's stream
+// One observable record of sigma_0 on the run's stream.  host_check = false skips the host-side
+// count check (graph capture: heom_batch_launch checks the counts per replay); the kernel keeps
+// the run's real max_records as its bound either way.
+int enqueue_record(heom_run *r, bool host_check = true);
 int io_range(heom_run *r, StateView state, int64_t u0, int64_t count, double *re, double *im, bool to_device);
 
 // the RK4 driver (propagate.cu)

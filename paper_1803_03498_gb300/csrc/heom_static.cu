@@ -1,13 +1,12 @@
 // heom_propagate_static: a propagation entry point that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured on its
-// stream (an allocation is not a capturable operation), plug-ins and embedded callers whose host
-// application owns every device allocation and hands the library no buffer, and latency-critical
-// paths where the implicit device synchronisation of cudaMalloc/cudaFree is not acceptable.  For
-// them the whole device workspace of one small propagation -- link tables, decay sums, the state
-// and the two intermediate RK4 copies the stage kernel works in, and the observable records --
-// lives in one file-scope device array owned by the library, of kStaticBytes bytes.  Every GPU that
-// loads the library holds that array until the process exits.
+// Some callers cannot call cudaMalloc: plug-ins and embedded callers whose host application owns
+// every device allocation and hands the library no buffer, and latency-critical paths where the
+// implicit device synchronisation of cudaMalloc/cudaFree is not acceptable.  For them the whole
+// device workspace of one small propagation -- link tables, decay sums, the state and the two
+// intermediate RK4 copies the stage kernel works in, and the observable records -- lives in one
+// file-scope device array owned by the library, of kStaticBytes bytes.  Every GPU that loads the
+// library holds that array until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -15,6 +14,7 @@
 
 #include "../../include/heom.h"
 #include "heom_internal.h"
+#include "heom_run.h"
 
 namespace heom {
 
@@ -94,10 +94,24 @@ extern "C" int heom_propagate_static(const heom_system *sys, const heom_hier *h,
   rc = heom_run_create(sys, h, precision, max_records, sigma0_re, sigma0_im, dip_w, ws, kStaticBytes, cuda_stream,
                        &r);
   --g_tune_suppress;
-  if (rc != HEOM_OK) return rc;
+  if (rc != HEOM_OK) {
+    // creation may have queued uploads into the array before it failed: let them finish before the
+    // lock is released, so that the next call does not reuse the array under them
+    cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(cuda_stream));
+    return rc;
+  }
   rc = heom_propagate(r, dt_fs, n_steps, obs_stride);
   if (rc == HEOM_OK) rc = heom_observables(r, records_out, cap_records, written);
   if (rc == HEOM_OK && sigma0_out_re && sigma0_out_im) rc = heom_get_sigma0(r, sigma0_out_re, sigma0_out_im);
+  if (rc != HEOM_OK) {
+    // on an error, stages may still be queued on the caller's stream and on the run's side stream
+    // (the FP64 head launches of a mixed run): wait for both before the array is released; the
+    // message of the first failure is kept
+    const std::string msg = heom_last_error();
+    if (r->side) cudaStreamSynchronize(r->side);
+    cudaStreamSynchronize(r->stream);
+    set_error(msg);
+  }
   heom_run_destroy(r);
   return rc;
 }

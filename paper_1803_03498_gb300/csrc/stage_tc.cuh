@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
   const uint32_t my_ld = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes of D
   uint32_t phase = 0;
   int failed = 0;
+  int pend_phase = -1;  // parity of a commit whose wait this thread gave up on (MMAs maybe in flight)
   int b = 0;
   for (int r = 0, chn = first; r < n_rounds; ++r, chn += nwarps, b ^= 1) {
     const bool valid = chn < n_chunks;  // warp-uniform
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
       while (!mbar_try_wait(mbar, phase)) {
         if (clock64() - t0 > kTcWaitCycles) {
           failed = 1;
+          pend_phase = (int)phase;
           break;
         }
       }
@@ -378,6 +380,15 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
   }
   cp_async_wait<0>();
   if (failed && threadIdx.x == 0 && c.err != nullptr) *c.err = 1;
+  // Tensor memory must not be freed under MMAs that may still write it.  A thread that gave up on a
+  // commit waits for it once more, again bounded; a thread whose wait on that commit succeeded saw
+  // those MMAs complete.  Every thread that issued no wait after its last success has nothing in
+  // flight: MMAs are issued only after the CTA barrier that precedes each round's wait.
+  if (pend_phase >= 0) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, (uint32_t)pend_phase) && clock64() - t0 <= kTcWaitCycles) {
+    }
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {

@@ -438,7 +438,10 @@ def propagate_static(system, rho0_re, rho0_im=None, precision="fp64", w=None, dt
     i0 = None if rho0_im is None else np.ascontiguousarray(rho0_im, dtype=np.float64)
     wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
     written = ctypes.c_int64()
-    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    if stream is None:  # the same default as Run: torch's current stream on the current device
+        import torch
+        stream = torch.cuda.current_stream()
+    st = ctypes.c_void_p(stream.cuda_stream)
     _check(L.heom_propagate_static(ctypes.byref(sa.s), hier._h, PRECISIONS[precision], _dp(r0), _dp(i0), _dp(wv),
                                    float(dt_fs), int(n_steps), int(obs_stride), st, _dp(rec), cap,
                                    ctypes.byref(written), _dp(s_re), _dp(s_im)))

@@ -1,13 +1,17 @@
-"""heom_propagate_static: the entry point for callers that cannot allocate device memory (code that
-runs while its stream is being captured into a CUDA graph, plug-ins whose host application owns
-all device allocations, latency-critical paths that cannot take the implicit synchronisation of
-cudaMalloc/cudaFree).  Its device workspace is the library's static 32 MiB array, so this test
-allocates nothing on the device for those calls either.
+"""heom_propagate_static: the entry point for callers that cannot allocate device memory (plug-ins
+whose host application owns all device allocations and hands the library no buffer, latency-critical
+paths that cannot take the implicit synchronisation of cudaMalloc/cudaFree).  Its device workspace is
+the library's static 32 MiB array, so this test allocates nothing on the device for those calls
+either.
 
-Checks, through the C ABI: several calls in a row (different sizes and precisions, so whatever an
-earlier call left in the shared array must not leak into the next) give the same records and final
-sigma_0 as the allocating path heom_run_create + heom_propagate + heom_observables, within the
-tolerance the parity tests use; a run above the 32 MiB limit is rejected with HEOM_E_NOMEM.
+Checks, through the C ABI: several calls in a row (different sizes, precisions and kernels -- the
+Hermitian and general matrix kernels, the split-TF32 tensor-core kernel and the general stage kernel
+of a two-exciton space -- so whatever an earlier call left in the shared array must not leak into the
+next) give the same records and final sigma_0 as the allocating path heom_run_create + heom_propagate
++ heom_observables, within the tolerance the parity tests use; the device's free memory does not
+change across calls; a run above the 32 MiB limit is rejected with HEOM_E_NOMEM; a call that fails
+after its run was set up (a time step beyond the RK4 stability bound) returns with no work pending on
+its stream, and the next call is unaffected.
 """
 import numpy as np
 import pytest
@@ -43,10 +47,23 @@ def static_path(heom, p, precision, steps, stride):
                                  n_steps=steps, obs_stride=stride)
 
 
+def _two_exciton_case():
+    """Three FMO-like sites in the two-exciton space (7 states, site-number bath couplings: the
+    general stage kernel), started in the first site's single-exciton state."""
+    pop, _ = wl.fmo_like()
+    s = pop.system
+    sub = wl.System("fmo-like 3 sites", np.asarray(s.H)[:3, :3], [0, 1, 2], [35.0] * 3, [166.0] * 3, [77.0] * 3,
+                    K=1, D=3)
+    g, _ = wl.two_exciton(sub)
+    re = np.zeros((g.N, g.N))
+    re[1, 1] = 1.0
+    return wl.Propagation(g, re, np.zeros_like(re), dt_fs=0.5, n_steps=40, tag="fmo-2x-3")
+
+
 def test_static_matches_allocating_path_on_consecutive_calls(heom):
     pop, dips = wl.fmo_like()
     cases = [(dips[0], "fp64", 40, 4), (wl.dimer(), "fp32_mixed", 300, 10), (pop, "fp32_mixed", 40, 5),
-             (dips[0], "fp64", 40, 4)]
+             (_two_exciton_case(), "fp64", 40, 5), (pop, "split_tf32", 40, 5), (dips[0], "fp64", 40, 4)]
     first = None
     for p, prec, steps, stride in cases:
         ref_obs, ref_s0 = allocating_path(heom, p, prec, steps, stride)
@@ -67,3 +84,41 @@ def test_static_rejects_runs_above_the_limit(heom):
         static_path(heom, p, "fp32_mixed", 1, 1)
     assert ei.value.code == heom.HEOM_E_NOMEM
     assert "32 MiB" in str(ei.value)
+
+
+def test_static_allocates_nothing(heom):
+    """After one warm-up call per case (the first launch of a kernel may load its code), further calls
+    leave the device's free memory and torch's allocations unchanged."""
+    import torch
+    pop, dips = wl.fmo_like()
+    cases = [(dips[0], "fp64", 20, 4), (pop, "fp32_mixed", 20, 5), (_two_exciton_case(), "fp32_mixed", 20, 5)]
+    for p, prec, steps, stride in cases:
+        static_path(heom, p, prec, steps, stride)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        for p, prec, steps, stride in cases:
+            static_path(heom, p, prec, steps, stride)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
+def test_static_error_path_leaves_nothing_pending(heom):
+    """dt far beyond the stability bound: heom_propagate refuses after the run was set up in the
+    array (uploads and the first record queued); the call returns with its stream idle, and the next
+    call gives the allocating path's result."""
+    import torch
+    pop, dips = wl.fmo_like()
+    p = dips[0]
+    with pytest.raises(heom.HeomError) as ei:
+        heom.propagate_static(p.system, p.rho0_re, p.rho0_im, precision="fp32_mixed", w=p.w, dt_fs=50.0,
+                              n_steps=10, obs_stride=1)
+    assert ei.value.code == heom.HEOM_E_ARG
+    assert torch.cuda.current_stream().query()
+    ref_obs, ref_s0 = allocating_path(heom, p, "fp64", 20, 4)
+    obs, s0 = static_path(heom, p, "fp64", 20, 4)
+    assert np.max(np.abs(obs - ref_obs)) <= FP64_TOL
+    assert np.max(np.abs(s0 - ref_s0)) <= FP64_TOL
