@@ -41,7 +41,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-FP64_PEAK_TFLOPS = 1.2  # measured FP64 FMA throughput of GB300 (152 SMs x 4 flop/clk x ~1.97 GHz)
+# GB300 issues 2 FP64 FMAs (4 flops) per clock per SM: the nominal 1.25 TFLOP/s at the 2.07 GHz
+# maximum SM clock over 152 SMs; a dependent-FMA probe on this GPU gave 1.199 TFLOP/s at ~1.97 GHz.
+FP64_FLOPS_PER_CLK_SM = 4.0
+FP64_PEAK_TFLOPS = 1.2  # fallback when no SM clock was sampled
+
+
+def fp64_peak_tflops(sm_mhz, n_sm=152):
+    """FP64 ALU peak at the SM clock the leg ran at (nvidia-smi median under load)."""
+    if not sm_mhz:
+        return FP64_PEAK_TFLOPS, "fallback 1.2 TFLOP/s (no clock sample)"
+    return n_sm * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12, f"{n_sm} SMs x 4 flop/clk x {sm_mhz:.0f} MHz"
 
 
 def _traffic():
@@ -184,15 +194,77 @@ def time_gpu(prop, precision, steps, warmup, ws, clocks=None, schedule=None):
     return ms, launches, kt, obs, clk
 
 
-def time_e2e(prop, precision, steps, hier):
-    """End to end through the public API with host buffers: run creation (tables and sigma_0 go
-    host -> device), `steps` RK4 steps, observables device -> host."""
+def fp64_and_gate(prop, gate_steps, warmup, ws, clocks):
+    """The FP64 path over the configuration's full length, and the mixed-precision error gate.
+
+    One FP64 run and one mixed run, both from rho(0), gate_steps RK4 steps with a population record
+    after every step.  The FP64 run's steps after the first `warmup` are device-timed (its ADO-RHS
+    evals/s and the per-launch time of its stage kernel); the gate is the largest population
+    difference between the two runs over all gate_steps + 1 records.  The FP64 GPU path itself is
+    held to the oracle by the parity tests (1e-12)."""
+    import torch
+
+    from paper_1803_03498_gb300 import heom
+
+    n_ado = prop.system.n_ado
+    run = heom.Run(prop.system, prop.rho0_re, prop.rho0_im, precision="fp64", w=prop.w, max_records=gate_steps + 2)
+    run.propagate(prop.dt_fs, warmup, 1)
+    torch.cuda.synchronize()
+    run.set_timing(True)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0.record(st)
+    run.propagate(prop.dt_fs, gate_steps - warmup, 1)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    _barrier(ws)
+    ms = _max_over_ranks(e0.elapsed_time(e1), ws)
+    timed = gate_steps - warmup
+    kt = run.kernel_time()
+    obs64 = run.observables()
+    sched = list(run.schedule(0))
+    run.close()
+    mixed = heom.Run(prop.system, prop.rho0_re, prop.rho0_im, precision="fp32_mixed", w=prop.w,
+                     max_records=gate_steps + 2)
+    mixed.propagate(prop.dt_fs, gate_steps, 1)
+    obs32 = mixed.observables()
+    mixed.close()
+    N = prop.system.N
+    assert obs64.shape == obs32.shape == (gate_steps + 1, N + 5)
+    pop_err = float(np.max(np.abs(obs32[:, :N] - obs64[:, :N])))
+    avg = kt["ms"] / max(kt["launches"], 1)
+    ach = kt["alg_flops"] / (kt["ms"] / 1000.0) / 1e12 if kt["ms"] > 0 else 0.0
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak, basis = fp64_peak_tflops(clk["sm_mhz"] if clk else None, n_sm)
+    leg = {"value": _job_value(ws, n_ado, timed, ms), "unit": UNIT, "ms_per_step": ms / timed, "steps": timed,
+           "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                        "peak_basis": basis,
+                        "flops": "4 N^3 per ADO (Hermitian form: H s only, s H = (H s)^dagger) + 8 N^2 "
+                                 "+ 8 (N-1) per up link + 8 (2N-1) per down link",
+                        "kernel": "stage_kernel<14,double,double>", "avg_launch_ms": avg, "schedule": sched},
+           "clocks": clk}
+    gate = {"steps": gate_steps, "records": gate_steps + 1, "max_pop_err": pop_err, "bar": 1e-6,
+            "pass": pop_err <= 1e-6,
+            "what": "max |population(mixed) - population(FP64)| over every RK4 step of the full-length run "
+                    "from rho(0), dt = 1 fs"}
+    return leg, gate
+
+
+def time_e2e(prop, precision, steps):
+    """End to end through the public API with host buffers: the hierarchy build (host), run creation
+    (tables and sigma_0 go host -> device), `steps` RK4 steps, observables device -> host."""
     import torch
 
     from paper_1803_03498_gb300 import heom
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    hier = heom.Hierarchy(prop.system.n_modes, prop.system.D)
     run = heom.Run(prop.system, prop.rho0_re, prop.rho0_im, precision=precision, w=prop.w,
                    max_records=steps + 2, hier=hier)
     run.propagate(prop.dt_fs, steps, 1)
@@ -263,7 +335,7 @@ def time_batch(steps=20, per_launch=10):
                      f"{t_capture:.2f} s)"}
 
 
-def time_field(steps=40, warmup=3):
+def time_field(steps=40, warmup=3, sm_mhz=None):
     """Pump-pulse propagation of the FMO-like two-exciton space (7 sites: 29 states, K = 1, D = 4:
     3060 ADOs of 29 x 29) on the general stage kernel: classic four-copy RK4 with H(t) at each stage
     time.  Device-timed steps; per-launch kernel time of the body launches; algorithmic flops per
@@ -305,8 +377,10 @@ def time_field(steps=40, warmup=3):
         if precision == "fp64":
             # body launches cover every ADO: one RHS evaluation each
             ach = flops_eval / (leg["avg_launch_ms"] / 1000.0) / 1e12
-            leg["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                               "frac": ach / FP64_PEAK_TFLOPS, "kernel": "gen_stage_kernel<double,double>"}
+            n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            peak, basis = fp64_peak_tflops(sm_mhz, n_sm)
+            leg["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                               "frac": ach / peak, "peak_basis": basis, "kernel": "gen_stage_kernel<double,double>"}
         out[precision] = leg
     return out
 
@@ -415,7 +489,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-field", action="store_true", help="skip the two-exciton laser-field leg")
-    ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 variant (0: steps/20)")
+    ap.add_argument("--gate-steps", type=int, default=1000,
+                    help="length of the FP64 run and of the mixed-vs-FP64 population gate (the configuration's "
+                         "1000 steps of 1 fs); its steps after the warm-up time the FP64 path (0: skip both)")
     ap.add_argument("--depth", type=int, default=0, help="override the hierarchy depth (profiling cases)")
     ap.add_argument("--tc-steps", type=int, default=0, help="timed steps of the split-TF32 variant (0: steps/10)")
     ap.add_argument("--only", default="", choices=["", "mixed", "fp64", "split_tf32", "dipole", "field"],
@@ -476,21 +552,15 @@ def main():
     value = _job_value(ws, n_ado, args.steps, ms_max)
     hbm_peak, peak_src = _peaks()
     traffic32, traffic64 = _traffic()
-    ach = kt["alg_bytes"] / (kt["ms"] / 1000.0) / 1e9 if kt["ms"] > 0 else 0.0
-    # the classic-RK4 per-unit figure (4 tile transfers of N^2 FP32 complex plus 2 M 4-byte link-table
-    # entries per ADO-RHS evaluation) x the body ADOs of one launch, for comparison with `frac`
+    avg_ms = kt["ms"] / max(kt["launches"], 1)
+    # algorithmic bytes of one body launch by the per-unit figure of the roofline (classic RK4: 4 tile
+    # transfers of N^2 FP32 complex elements plus 2 M 4-byte link-table entries per ADO-RHS evaluation)
+    # x the body ADOs of one launch; the Horner form of RK4 moves 2.75 tile transfers per evaluation,
+    # reported beside it as the stricter count
     nb = n_ado - (1 + prop.system.n_modes)
     unit4 = nb * (4.0 * prop.system.N ** 2 * 8 + 2 * prop.system.n_modes * 4)
-
-    # FP64 variant
-    f64_steps = args.fp64_steps or max(3, args.steps // 20)
-    ms64, l64, kt64, obs64, _ = time_gpu(prop, "fp64", f64_steps, 3, ws, None)
-    ms64 = _max_over_ranks(ms64, ws)
-    v64 = _job_value(ws, n_ado, f64_steps, ms64)
-    ach64 = kt64["alg_flops"] / (kt64["ms"] / 1000.0) / 1e12 if kt64["ms"] > 0 else 0.0
-    n = prop.system.N
-    k = min(obs.shape[0], obs64.shape[0])
-    pop_diff = float(np.max(np.abs(obs[:k, :n] - obs64[:k, :n])))  # same start, same first steps
+    ach = unit4 / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else 0.0
+    ach_horner = kt["alg_bytes"] / (kt["ms"] / 1000.0) / 1e9 if kt["ms"] > 0 else 0.0
 
     # split-TF32 variant: the commutator of the FP32 body on the tensor cores (tcgen05)
     tc_steps = args.tc_steps or max(3, args.steps // 10)
@@ -498,12 +568,19 @@ def main():
     ms_tc = _max_over_ranks(ms_tc, ws)
     v_tc = _job_value(ws, n_ado, tc_steps, ms_tc)
     ach_tc = kt_tc["alg_bytes"] / (kt_tc["ms"] / 1000.0) / 1e9 if kt_tc["ms"] > 0 else 0.0
-    k = min(obs_tc.shape[0], obs64.shape[0])
-    pop_diff_tc = float(np.max(np.abs(obs_tc[:k, :n] - obs64[:k, :n])))
+    n = prop.system.N
+    k = min(obs_tc.shape[0], obs.shape[0])
+    pop_diff_tc = float(np.max(np.abs(obs_tc[:k, :n] - obs[:k, :n])))
+
+    # FP64 over the configuration's full length, and the mixed-vs-FP64 population gate
+    fp64, gate = None, None
+    if args.gate_steps > 0:
+        fp64, gate = fp64_and_gate(prop, args.gate_steps, 3, ws, clocks)
+        fp64["mixed_over_fp64"] = value / fp64["value"]
+        fp64["roofline"]["traffic"] = traffic64
 
     # end to end through the public API (host buffers)
-    hier = heom.Hierarchy(prop.system.n_modes, prop.system.D)
-    t_e2e, h2d, d2h = time_e2e(prop, "fp32_mixed", args.steps, hier)
+    t_e2e, h2d, d2h = time_e2e(prop, "fp32_mixed", args.steps)
     t_e2e = _max_over_ranks(t_e2e, ws)
     e2e_value = _job_value(ws, n_ado, args.steps, 1000.0 * t_e2e)
 
@@ -521,38 +598,37 @@ def main():
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                          "frac": ach / hbm_peak, "traffic": traffic32,
-                         "alg_bytes_per_launch": kt["alg_bytes"] / max(kt["launches"], 1),
-                         "frac_per_unit_4_tiles": unit4 / (kt["ms"] / max(kt["launches"], 1) / 1000.0) / 1e9 / hbm_peak,
+                         "alg_bytes_per_launch": unit4,
+                         "alg_bytes": "per-unit figure: 4 N^2 x 8 B + 2 M x 4 B per ADO-RHS evaluation x the body ADOs",
+                         "frac_horner": ach_horner / hbm_peak,
+                         "alg_bytes_per_launch_horner": kt["alg_bytes"] / max(kt["launches"], 1),
                          "kernel": "stage_kernel<14,float,float> (levels >= 2)",
-                         "peak_source": peak_src, "timed_launches": kt["launches"],
-                         "avg_launch_ms": kt["ms"] / max(kt["launches"], 1),
+                         "peak_source": peak_src, "timed_launches": kt["launches"], "avg_launch_ms": avg_ms,
                          "schedule": kt["schedule"]},
-            "fp64": {"value": v64, "unit": UNIT, "steps": f64_steps, "ms_per_step": ms64 / f64_steps,
-                     "mixed_over_fp64": value / v64,
-                     "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                  "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": traffic64,
-                                  "kernel": "stage_kernel<14,double,double>",
-                                  "avg_launch_ms": kt64["ms"] / max(kt64["launches"], 1),
-                                  "schedule": kt64["schedule"]}},
             "split_tf32": {"value": v_tc, "unit": UNIT, "steps": tc_steps, "ms_per_step": ms_tc / tc_steps,
-                           "pop_diff_vs_fp64": pop_diff_tc,
+                           "pop_diff_vs_mixed": pop_diff_tc,
                            "roofline": {"bound": "hbm", "achieved": ach_tc, "peak": hbm_peak, "unit": "GB/s",
                                         "frac": ach_tc / hbm_peak, "traffic": None,
                                         "kernel": "stage_tc_kernel<14> (tcgen05.mma kind::tf32, levels >= 2)",
                                         "avg_launch_ms": kt_tc["ms"] / max(kt_tc["launches"], 1),
                                         "schedule": kt_tc["schedule"]}},
-            "mixed_vs_fp64_pop_diff": pop_diff,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "what": "heom_run_create from host arrays + propagate + observables to host, wall clock"},
+                    "what": "hierarchy build + heom_run_create from host arrays + propagate + observables to host, "
+                            "wall clock"},
         }
         if not args.no_batch:
             line["batch"] = time_batch()
         if not args.no_field:
-            line["two_exciton_field"] = time_field()
+            line["two_exciton_field"] = time_field(sm_mhz=(fp64 or {}).get("clocks", {}).get("sm_mhz")
+                                                   or (clk or {}).get("sm_mhz"))
         if not args.no_serving and ws == 1:
             line["serving"] = time_serving()
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prop)
+        # the FP64 half of the metric and the mixed-precision gate close the line
+        if gate is not None:
+            line["mixed_vs_fp64_1000_steps"] = gate
+            line["fp64"] = fp64
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

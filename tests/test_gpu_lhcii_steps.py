@@ -81,7 +81,8 @@ def test_lhcii_family_fp64_every_ado(oracle_runs, which):
     assert p.system.n_ado == 35960
     ref, oobs = oracle_runs[which]
     r, gobs = gpu_run(p, "fp64", stride=1)
-    assert gobs.shape == oobs.shape == (STEPS + 1, p.system.N + 5)
+    # GPU records carry a Hermiticity column after the oracle's N + 4 values
+    assert gobs.shape == (STEPS + 1, p.system.N + 5) and oobs.shape == (STEPS + 1, p.system.N + 4)
     re, im = r.get_ados(0, r.n_ado)
     err = np.max(np.abs(re + 1j * im - ref))
     assert err <= FP64_TOL, err
