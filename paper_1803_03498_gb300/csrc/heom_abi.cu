@@ -31,6 +31,7 @@ int launch_stage(int precision, const StageCommon &c, double ch, const double *t
       {launch_stage_fp32_a, launch_stage_fp32_b, launch_stage_fp32_c, launch_stage_fp32_d},
       {launch_stage_head_a, launch_stage_head_b, launch_stage_head_c, launch_stage_head_d}};
   int rc = 1;
+  if (precision == 0 && c.herm && !c.cplx_h) rc = launch_stage_col(c, ch, term, H, st, sm_count);
   for (int g = 0; g < 4 && rc == 1; ++g) rc = fns[precision][g](c, ch, term, H, Hi, st, sm_count);
   if (rc == 1) {
     set_error("stage kernel: n_states not compiled");

@@ -165,6 +165,12 @@ struct GenArgs {
 int launch_stage_gen(int kind, const StageCommon &c, StateView base2, StateView out2, double c1, double c2,
                      const double *H, const double *Hi, const double *T, cudaStream_t st, int sm_count);
 
+// Column-form FP64 stage kernel (stage_col.cuh) for Hermitian runs with a real H and 8 <= n <= 16:
+// every lane of a warp owns one column of one part of an ADO's result, so all 32 lanes do FP64 work.
+// Returns 1 when it does not cover n.
+int launch_stage_col(const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
+                     int sm_count);
+
 // precision: 0 = FP64 (compute and storage double), 1 = mixed body (float, float), 2 = mixed head
 // (compute double, body storage float).
 int launch_stage(int precision, const StageCommon &c, double ch, const double *term, const double *H,

@@ -248,3 +248,29 @@ def test_state_roundtrip_and_errors():
         assert ei.value.code == heom.HEOM_E_ARG
         with pytest.raises(heom.HeomError):
             r.get_ados(r.n_ado - 1, 2)
+
+
+@pytest.mark.parametrize("N,K,D", [(8, 1, 3), (9, 0, 4), (11, 1, 2), (13, 0, 3), (16, 1, 2)])
+def test_column_kernel_sizes_fp64(N, K, D):
+    """FP64 Hermitian runs with 8 <= N <= 16 take the column-form stage kernel (every lane owns one
+    column of one part of an ADO's result).  Seeded symmetric H, one bath per site, population run from
+    the first site: every element of every ADO after 30 steps within 1e-12 of the oracle.  The sizes
+    give ragged last chunks, ADOs with more links than one record batch (up to 2M up links at the
+    root) and one-ADO chunks (N = 16)."""
+    rng = np.random.default_rng(1803100 + N)
+    H = _sym(rng, N)
+    s = wl.System(f"column N={N}", H, list(range(N)), [35.0] * N, [60.0] * N, [300.0] * N, K=K, D=D)
+    rho = np.zeros((N, N))
+    rho[0, 0] = 1.0
+    p = wl.Propagation(s, rho, np.zeros((N, N)), 1.0, 30)
+    m, ore, oim, oobs = oracle_propagate(p, p.n_steps, stride=3)
+    r, gobs = gpu_run(p, "fp64", stride=3)
+    ref = ore + 1j * oim
+    assert np.max(np.abs(full_state(r) - ref)) <= FP64_TOL
+    assert np.max(np.abs(gobs[:, :N + 4] - oobs[:, :N + 4])) <= FP64_TOL
+    assert np.max(np.abs(ref[-1])) > 0  # the deepest ADOs were reached
+
+
+def _sym(rng, N):
+    H = np.diag(rng.uniform(0.0, 400.0, N)) + np.triu(rng.normal(0.0, 40.0, (N, N)), 1)
+    return H + np.triu(H, 1).T
