@@ -34,6 +34,8 @@ extern "C" {
 #define HEOM_E_TIMEOUT (-5)  /* a bounded device-side wait gave up */
 #define HEOM_E_NUMERIC (-6)  /* NaN/Inf detected in the root ADO */
 #define HEOM_E_STATE (-7)    /* call not valid for the handle's current state */
+#define HEOM_E_BOUNDS (-8)   /* debug build only (compiled with -DHEOM_DEBUG): a stage kernel found a link
+                                record naming an ADO, a state or a record range outside the run */
 
 /* Arithmetic of a run. */
 #define HEOM_FP64 0       /* every ADO stored and computed in FP64 */
@@ -218,7 +220,9 @@ int heom_record_len(const heom_run *r);
  * heom_observables -- synchronises the run's stream and copies up to cap_records records (the
  * first record is the state at creation, then one per obs_stride steps) into out
  * ([cap_records][heom_record_len]); *written = records copied.  HEOM_E_NUMERIC if a record
- * holds NaN/Inf.
+ * holds NaN/Inf; HEOM_E_TIMEOUT if a bounded device-side wait gave up; HEOM_E_BOUNDS if a bounds
+ * check of a debug build failed.  The record's content is fixed (see heom_record_len): the dipole
+ * weights of the correlation are set once at heom_run_create.
  */
 int heom_observables(heom_run *r, double *out, int64_t cap_records, int64_t *written);
 

@@ -15,6 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.environ.get("HEOM_CSRC_DIR") or os.path.join(HERE, "csrc")
 OUT = os.environ.get("HEOM_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libheom.so")
+# the bounds-checked debug build (-DHEOM_DEBUG): every link record's neighbour, state and record range
+# is checked in the stage kernels before use, and a failure is reported by heom_observables
+DEBUG_OUT = os.path.join(HERE, "_build_debug")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = (["hierarchy.cpp", "heom_abi.cu", "propagate.cu", "tuner.cu", "batch.cu", "aux_kernels.cu", "heom_static.cu"]
            + [f"stage_{p}_{g}.cu" for p in ("fp64", "fp32", "head") for g in "abcd"]
@@ -31,8 +34,10 @@ def _nvcc():
     return "nvcc"
 
 
-def _flags():
+def _flags(debug=False):
     extra = os.environ.get("HEOM_NVCC_DEFINES", "").split()  # e.g. -DHEOM_STAGE_WARPS=8 (tuning builds)
+    if debug:
+        extra = extra + ["-DHEOM_DEBUG"]
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                    "-I", os.path.join(ROOT, "include"), "-I", os.path.join(HERE, "csrc"),
                    "--expt-relaxed-constexpr"] + extra
@@ -45,19 +50,23 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
+    """Compile and link libheom.so; debug=True builds the bounds-checked variant into _build_debug/
+    (load it with HEOM_LIB=<path> in the environment).  Returns the library's path."""
+    out = DEBUG_OUT if debug else OUT
+    lib = os.path.join(out, "libheom.so")
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "heom.h")]
     objs, work = [], []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OUT, s + ".o")
+        obj = os.path.join(out, s + ".o")
         objs.append(obj)
         if _stale(obj, [src] + hdrs + [__file__]):
-            cmd = [nvcc] + _flags() + ["-c", src, "-o", obj]
+            cmd = [nvcc] + _flags(debug) + ["-c", src, "-o", obj]
             if s.endswith(".cpp"):
-                cmd = [nvcc] + _flags() + ["-x", "cu", "-c", src, "-o", obj]
+                cmd = [nvcc] + _flags(debug) + ["-x", "cu", "-c", src, "-o", obj]
             work.append(cmd)
     with cf.ThreadPoolExecutor(max_workers=jobs or max(1, min(len(work), os.cpu_count() or 1))) as ex:
         futs = [ex.submit(subprocess.run, cmd, capture_output=True, text=True) for cmd in work]
@@ -67,16 +76,16 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
                 sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed: {cmd[-3]}")
-    if work or not os.path.exists(LIB) or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if work or not os.path.exists(lib) or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             raise RuntimeError("link of libheom.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_
   __syncthreads();
   const LinkRec<CT> *recs = reinterpret_cast<const LinkRec<CT> *>(kOwnHead ? c.recs_head : c.recs_body);
   const int64_t rbase = kOwnHead ? 0 : c.rec_split;
+  const int64_t rlim = kOwnHead ? c.rec_split : c.n_recs;  // records [rbase, rlim) of this region
   const bool has_b1 = c.y.head != nullptr || c.y.body != nullptr;
   const bool has_o2 = a.out2.head != nullptr || a.out2.body != nullptr;
   const bool has_b2 = a.base2.head != nullptr || a.base2.body != nullptr;
@@ -154,12 +155,14 @@ __global__ void __launch_bounds__(kGenWarps * 32) gen_stage_kernel(const __grid_
     for (int64_t base = lo; base < hi; base += 32) {
       const int cnt = (int)min((int64_t)32, hi - base);
       LinkRec<CT> mine{};
-      if (lane < cnt) mine = recs[base + lane - rbase];
+      mine.v = -1;
+      if (lane < cnt && HEOM_IN_RANGE(c.err, base + lane, rbase, rlim)) mine = recs[base + lane - rbase];
 #pragma unroll 4
       for (int k = 0; k < cnt; ++k) {
         const int v = __shfl_sync(0xffffffffu, mine.v, k);
         const int s = __shfl_sync(0xffffffffu, mine.s, k) & kRecStateMask;
         const CT rre = __shfl_sync(0xffffffffu, mine.re, k), rim = __shfl_sync(0xffffffffu, mine.im, k);
+        if (!HEOM_IN_RANGE(c.err, v, 0, c.n_ado) || !HEOM_IN_RANGE(c.err, s, 0, N)) continue;
         if (lj && s >= i0 && s < i1) {  // row part: element (s, j) += R v_sj (lane j, column j of R)
           const C2 vs = gen_load<CT, BT>(c.zin, E, Ep, c.u_split, v, s * N + j);
           C2 &rs = R[s * N + j];

@@ -603,6 +603,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     }
   }
   loff[h.n] = nlink;
+  r->n_links = nlink;
   r->rec_split = loff[r->u_split];
 
   {  // algorithmic bytes and flops of one launch of the dominant kernel (ADOs u >= u_split)

@@ -14,6 +14,39 @@ constexpr int kMaxStates = 24;
 
 void set_error(const std::string &msg);
 
+// Device error word of a run (StageCommon::err): bit 0 -- a bounded device-side wait gave up (the
+// tensor-core kernel); bit 1 -- a bounds check of the debug build failed.  heom_observables reports
+// them as HEOM_E_TIMEOUT and HEOM_E_BOUNDS.
+constexpr int kErrTimeout = 1;
+constexpr int kErrBounds = 2;
+
+// Debug build (compiled with -DHEOM_DEBUG): every neighbour index a link record names, its coupled
+// state and every record range a stage kernel reads are checked before use; an index outside its
+// range sets kErrBounds in the run's error word and the access is skipped.  Without HEOM_DEBUG the
+// check is the constant true and costs nothing.
+#ifdef HEOM_DEBUG
+__device__ __forceinline__ bool heom_in_range(int *err, int64_t idx, int64_t lo, int64_t hi) {
+  if (idx >= lo && idx < hi) return true;
+  if (err) atomicOr(err, kErrBounds);
+  return false;
+}
+#define HEOM_IN_RANGE(err, idx, lo, hi) heom_in_range((err), (int64_t)(idx), (int64_t)(lo), (int64_t)(hi))
+#else
+#define HEOM_IN_RANGE(err, idx, lo, hi) true
+#endif
+
+// A batch of nr link records starting at record lo, read from a region that holds records
+// [rbase, limit): nr, or 0 (and kErrBounds) when the debug build finds the batch outside the region.
+__device__ __forceinline__ int heom_rec_batch(int *err, int64_t lo, int nr, int64_t rbase, int64_t limit) {
+#ifdef HEOM_DEBUG
+  if (lo < rbase || nr < 0 || lo + nr > limit) {
+    if (err) atomicOr(err, kErrBounds);
+    return 0;
+  }
+#endif
+  return nr;
+}
+
 // One link of an ADO u to a neighbour v = n(u) +- e_l through a mode l of state s.  Only row s and
 // column s of v contribute to row s and column s of d sigma_u / dt: element (s, j != s) with
 // coefficient R, element (i != s, s) with conj(R), element (s, s) with 2 Re R, where
@@ -62,7 +95,8 @@ struct StageCommon {
   int n;
   int cplx_h;           // H has an imaginary part
   int herm;             // every ADO is Hermitian: gather row s only, and s H = (H s)^dagger
-  int *err;             // device flag: a bounded device-side wait gave up (tensor-core kernel)
+  int *err;             // device error word (kErrTimeout, kErrBounds)
+  int64_t n_recs;       // link records in all (link_off[n_ado]); the debug build checks ranges against it
   int occ_pct;          // schedule: grid sized for this percentage of the CTAs that fit on an SM
   int cpw;              // schedule: column-0 kernels' chunks per warp step (1, 2, 4)
 };

@@ -68,6 +68,7 @@ struct heom_run {
   void *recs_head = nullptr;         // LinkRec<double>, ADOs u < u_split
   void *recs_body = nullptr;         // LinkRec<float or double>, ADOs u >= u_split
   int64_t rec_split = 0;             // link_off[u_split]
+  int64_t n_links = 0;               // link_off[n_ado]: link records in all
   double *gsum = nullptr;
   double *records = nullptr;         // [max_records][n + 5]
   double *w_dev = nullptr;           // [n] dipole weights (zeros if none)

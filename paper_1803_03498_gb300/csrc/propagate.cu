@@ -37,6 +37,7 @@ StageCommon heom::common_for(const heom_run *r, StateView zin, StateView y, Stat
   c.cplx_h = r->cplx_h ? 1 : 0;
   c.herm = r->herm ? 1 : 0;
   c.err = r->err_dev;
+  c.n_recs = r->n_links;
   return c;
 }
 
@@ -282,6 +283,11 @@ extern "C" int heom_observables(heom_run *r, double *out, int64_t cap_records, i
   if (e != cudaSuccess) return cuda_fail("heom_observables: counter", e);
   int err_flag = 0;
   std::memcpy(&err_flag, &cnt_err[1], sizeof(int));
+  if (err_flag & kErrBounds) {
+    set_error("heom_observables: a bounds check of the debug build failed (a link record names an ADO, state or "
+              "record range outside the run; its results are invalid)");
+    return HEOM_E_BOUNDS;
+  }
   if (err_flag) {
     set_error("heom_observables: a device-side wait of the tensor-core stage kernel gave up (its results are invalid)");
     return HEOM_E_TIMEOUT;

@@ -86,12 +86,13 @@ __device__ __forceinline__ void col_load_recs(const LinkRec<double> *recs, int64
 
 // Row s of the neighbour of each of the nr records into gbuf[r][0..N), one cp.async group.
 template <int N>
-__device__ __forceinline__ void col_gather(const double2 *zin, int Ep, const LinkRec<double> *rec, int nr,
-                                           double2 *gbuf, int lane) {
+__device__ __forceinline__ void col_gather(const StageCommon &c, const double2 *zin, int Ep, const LinkRec<double> *rec,
+                                           int nr, double2 *gbuf, int lane) {
   for (int t = lane; t < nr * N; t += 32) {
     const int r = t / N, k = t - r * N;
     const int s = rec[r].s & kRecStateMask;
-    col_cp16(gbuf + r * N + k, zin + (int64_t)rec[r].v * Ep + s * N + k);
+    if (HEOM_IN_RANGE(c.err, rec[r].v, 0, c.n_ado) && HEOM_IN_RANGE(c.err, s, 0, N))
+      col_cp16(gbuf + r * N + k, zin + (int64_t)rec[r].v * Ep + s * N + k);
   }
   col_commit();
 }
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(ColShape<N>::WARPS * 32) stage_col_kernel(cons
       int nrf0 = 0, nrf1 = 0;
       for (int f = fa, k = 0; f < fb; ++f, ++k) {
         const int64_t lo = __shfl_sync(0xffffffffu, off, f), hi = __shfl_sync(0xffffffffu, off, f + 1);
-        const int nr = (int)min(hi - lo, (int64_t)RB);
+        const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)RB), 0, c.n_recs);
         if (k == 0) nrf0 = nr;
         else nrf1 = nr;
         col_load_recs(recs, lo, nr, recb + k * RB, lane);
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(ColShape<N>::WARPS * 32) stage_col_kernel(cons
       col_wait_all();
       __syncwarp();
       for (int f = fa, k = 0; f < fb; ++f, ++k)
-        col_gather<N>(zin, Ep, recb + k * RB, k == 0 ? nrf0 : nrf1, gbuf + k * RB * N, lane);
+        col_gather<N>(c, zin, Ep, recb + k * RB, k == 0 ? nrf0 : nrf1, gbuf + k * RB * N, lane);
       if (act) {
         // p = 0: Q_re = H Im s + coef Re s;  p = 1: Q_im = -H Re s + coef Im s
         double src[N], own[N];
@@ -224,11 +225,11 @@ __global__ void __launch_bounds__(ColShape<N>::WARPS * 32) stage_col_kernel(cons
         col_links<N>(recb + k * RB, nr0, gbuf + k * RB * N, qs, lane);
         for (int64_t blo = lo + nr0; blo < hi; blo += RB) {  // further record batches
           __syncwarp();
-          const int nr = (int)min(hi - blo, (int64_t)RB);
+          const int nr = heom_rec_batch(c.err, blo, (int)min(hi - blo, (int64_t)RB), 0, c.n_recs);
           col_load_recs(recs, blo, nr, recb + k * RB, lane);
           col_wait_all();
           __syncwarp();
-          col_gather<N>(zin, Ep, recb + k * RB, nr, gbuf + k * RB * N, lane);
+          col_gather<N>(c, zin, Ep, recb + k * RB, nr, gbuf + k * RB * N, lane);
           col_wait_all();
           __syncwarp();
           col_links<N>(recb + k * RB, nr, gbuf + k * RB * N, qs, lane);

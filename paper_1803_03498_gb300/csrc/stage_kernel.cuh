@@ -185,13 +185,15 @@ __device__ __forceinline__ void issue_gathers(const StageCommon &c, const LinkRe
     for (int t0 = lane; t0 < nrec * P; t0 += 32) {
       const int sl = t0 / P, pc = t0 - sl * P;
       const int s = rec[sl].s & kRecStateMask;
-      gather_piece<N, CT, BT, PW>(c, rec[sl].v, s * N + pc * PW, gbuf + sl * N + pc * PW);
+      if (HEOM_IN_RANGE(c.err, rec[sl].v, 0, c.n_ado) && HEOM_IN_RANGE(c.err, s, 0, N))
+        gather_piece<N, CT, BT, PW>(c, rec[sl].v, s * N + pc * PW, gbuf + sl * N + pc * PW);
     }
   } else {
     constexpr int per = P + N;
     for (int t0 = lane; t0 < nrec * per; t0 += 32) {
       const int sl = t0 / per, el = t0 - sl * per;
       const int s = rec[sl].s & kRecStateMask;
+      if (!HEOM_IN_RANGE(c.err, rec[sl].v, 0, c.n_ado) || !HEOM_IN_RANGE(c.err, s, 0, N)) continue;
       if (el < P) gather_piece<N, CT, BT, PW>(c, rec[sl].v, s * N + el * PW, gbuf + sl * 2 * N + el * PW);
       else gather_piece<N, CT, BT, 1>(c, rec[sl].v, (el - P) * N + s, gbuf + sl * 2 * N + N + (el - P));
     }
@@ -317,9 +319,10 @@ __device__ __forceinline__ void owner_apply(const StageCommon &c, const LinkRec<
                                             CT (&rr)[N], CT (&ri)[N]) {
   using R = LinkRec<CT>;
   owner_links<N, CT>(rec, nrec, u0, lane, tb, gbuf, rr, ri);
+  const int64_t rlim = StageShape<N, CT, BT>::kOwnHead ? c.rec_split : c.n_recs;
   for (int64_t blo = lo + nrec; blo < hi; blo += cap) {  // further link batches
     __syncwarp();
-    const int nr = (int)min(hi - blo, (int64_t)cap);
+    const int nr = heom_rec_batch(c.err, blo, (int)min(hi - blo, (int64_t)cap), rbase, rlim);
     warp_copy16(rec, recs + (blo - rbase), nr * (int)sizeof(R), lane);
     cp_async_commit();
     cp_async_wait<0>();
@@ -454,6 +457,7 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
   const C2 *y_own = S::kOwnHead ? reinterpret_cast<const C2 *>(c.y.head) : reinterpret_cast<const C2 *>(c.y.body);
   const R *recs = reinterpret_cast<const R *>(S::kOwnHead ? c.recs_head : c.recs_body);
   const int64_t rbase = S::kOwnHead ? 0 : c.rec_split;
+  const int64_t rlim = S::kOwnHead ? c.rec_split : c.n_recs;  // records [rbase, rlim) of this region
   const int own0 = S::kOwnHead ? 0 : c.u_split;
 
   const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
@@ -474,7 +478,7 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
     const int cnt = min(A, c.u_end - u0);
     issue_tiles<N, CT, BT>(zin_own, own0, u0, cnt, wb + W::tile0, lane);
     const int64_t lo = __shfl_sync(0xffffffffu, off_cur, 0), hi = __shfl_sync(0xffffffffu, off_cur, cnt);
-    const int nr = (int)min(hi - lo, (int64_t)cap);
+    const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)cap), rbase, rlim);
     warp_copy16(wb + W::rec0, recs + (lo - rbase), nr * (int)sizeof(R), lane);
     cp_async_commit();
   }
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
       const int vcnt = min(A, c.u_end - v0);
       issue_tiles<N, CT, BT>(zin_own, own0, v0, vcnt, wb + (b ? W::tile0 : W::tile1), lane);
       const int64_t lo = __shfl_sync(0xffffffffu, off_nxt, 0), hi = __shfl_sync(0xffffffffu, off_nxt, vcnt);
-      const int nr = (int)min(hi - lo, (int64_t)cap);
+      const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)cap), rbase, rlim);
       warp_copy16(wb + (b ? W::rec0 : W::rec1), recs + (lo - rbase), nr * (int)sizeof(R), lane);
     }
     cp_async_commit();
@@ -646,7 +650,7 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
       apply_links<N, CT, BT>(rec, lo, nrec, my_lo, my_hi, active, li, herm, ot, gbuf);
       for (int64_t blo = lo + nrec; blo < hi; blo += cap) {  // further link batches
         __syncwarp();
-        const int nr = (int)min(hi - blo, (int64_t)cap);
+        const int nr = heom_rec_batch(c.err, blo, (int)min(hi - blo, (int64_t)cap), rbase, rlim);
         warp_copy16(rec, recs + (blo - rbase), nr * (int)sizeof(R), lane);
         cp_async_commit();
         cp_async_wait<0>();

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
     const int cnt = min(A, c.u_end - u0);
     issue_tiles<N, float, float>(zin_own, own0, u0, cnt, wb + W::tile0, lane);
     const int64_t lo = __shfl_sync(0xffffffffu, off_cur, 0), hi = __shfl_sync(0xffffffffu, off_cur, cnt);
-    const int nr = (int)min(hi - lo, (int64_t)cap);
+    const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)cap), rbase, c.n_recs);
     warp_copy16(wb + W::rec0, recs + (lo - rbase), nr * (int)sizeof(R), lane);
     cp_async_commit();
   }
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
       const int vcnt = min(A, c.u_end - v0);
       issue_tiles<N, float, float>(zin_own, own0, v0, vcnt, wb + (b ? W::tile0 : W::tile1), lane);
       const int64_t lo = __shfl_sync(0xffffffffu, off_nxt, 0), hi = __shfl_sync(0xffffffffu, off_nxt, vcnt);
-      const int nr = (int)min(hi - lo, (int64_t)cap);
+      const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)cap), rbase, c.n_recs);
       warp_copy16(wb + (b ? W::rec0 : W::rec1), recs + (lo - rbase), nr * (int)sizeof(R), lane);
     }
     cp_async_commit();
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
     off_nxt = off_nx2;
   }
   cp_async_wait<0>();
-  if (failed && threadIdx.x == 0 && c.err != nullptr) *c.err = 1;
+  if (failed && threadIdx.x == 0 && c.err != nullptr) atomicOr(c.err, kErrTimeout);
   // Tensor memory must not be freed under MMAs that may still write it.  A thread that gave up on a
   // commit waits for it once more, again bounded; a thread whose wait on that commit succeeded saw
   // those MMAs complete.  Every thread that issued no wait after its last success has nothing in

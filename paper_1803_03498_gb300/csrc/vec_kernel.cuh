@@ -86,6 +86,7 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
   const bool has_y = (c.y.head != nullptr) || (c.y.body != nullptr);
   const LinkRec<CT> *recs = reinterpret_cast<const LinkRec<CT> *>(kOwnHead ? c.recs_head : c.recs_body);
   const int64_t rbase = kOwnHead ? 0 : c.rec_split;
+  const int64_t rlim = kOwnHead ? c.rec_split : c.n_recs;  // records [rbase, rlim) of this region
   const int u0 = c.u_begin + step * SA;
   const int cnt = min(SA, c.u_end - u0);
   C2 x[GE], yv[GE];
@@ -137,7 +138,8 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
 #pragma unroll
       for (int q = 0; q < GE; ++q) {
         const int64_t t = base + q * 32 + lane;
-        if (t < hi) rq[q] = recs[t - rbase];
+        rq[q].v = -1;
+        if (t < hi && HEOM_IN_RANGE(c.err, t, rbase, rlim)) rq[q] = recs[t - rbase];
       }
       int owner[GE];
       CT cr[GE], ci[GE];
@@ -147,7 +149,8 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
         owner[q] = -1;
         cr[q] = 0;
         ci[q] = 0;
-        if (t < hi) {
+        if (t < hi && HEOM_IN_RANGE(c.err, rq[q].v, 0, c.n_ado) &&
+            HEOM_IN_RANGE(c.err, rq[q].s & kRecStateMask, 0, N)) {
           const int st = rq[q].s & kRecStateMask;
           const int o = ((rq[q].s >> 8) - u0) & 31;
           const int og = o / A;

@@ -12,10 +12,12 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libheom.so")
+# HEOM_LIB selects another build of the same library (the bounds-checked debug build of build(debug=True))
+LIB_PATH = os.environ.get("HEOM_LIB") or os.path.join(_HERE, "_build", "libheom.so")
 
 HEOM_OK = 0
-HEOM_E_ARG, HEOM_E_OVERFLOW, HEOM_E_NOMEM, HEOM_E_CUDA, HEOM_E_TIMEOUT, HEOM_E_NUMERIC, HEOM_E_STATE = range(-1, -8, -1)
+(HEOM_E_ARG, HEOM_E_OVERFLOW, HEOM_E_NOMEM, HEOM_E_CUDA, HEOM_E_TIMEOUT, HEOM_E_NUMERIC, HEOM_E_STATE,
+ HEOM_E_BOUNDS) = range(-1, -9, -1)
 FP64, FP32_MIXED, SPLIT_TF32 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED, "split_tf32": SPLIT_TF32}
 

@@ -4,6 +4,9 @@ C ABI; every step of every propagation runs in libheom's kernels).
 A request is one propagation (system, rho(0), dt, steps).  The server
   * admits arrived requests first-fit while their device workspace (heom_run_bytes) fits the remaining
     memory budget; a request larger than the whole budget is rejected at once (it can never run);
+  * builds each admitted request's run (link records on the host, uploads, the CUDA graph) on a pool
+    of `workers` host threads -- the library releases the interpreter lock, so several runs are set
+    up at once while the main loop keeps launching;
   * gives every admitted request its own CUDA stream and advances it by `quantum` RK4 steps at a time
     (replays of a CUDA graph of `graph_steps` steps captured at admission, by default the whole
     quantum: one launch on the host per quantum), so
@@ -19,6 +22,7 @@ from __future__ import annotations
 
 import time
 from collections import deque
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -82,7 +86,8 @@ class ServeStats:
 
 class Server:
     def __init__(self, budget_bytes: float = 120e9, precision: str = "fp32_mixed", quantum: int = 100,
-                 max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False, graph_steps: int | None = None):
+                 max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False, graph_steps: int | None = None,
+                 workers: int = 4):
         if obs_stride > 0 and quantum % obs_stride:
             raise ValueError("obs_stride must divide quantum")
         if graph_steps is None:  # one graph per quantum (measured: fewer, longer graphs serve more)
@@ -96,6 +101,7 @@ class Server:
         self.obs_stride = int(obs_stride)
         self.keep_sigma0 = keep_sigma0
         self.graph_steps = int(graph_steps)
+        self.workers = max(0, int(workers))
         self._hier_cache = {}
 
     def _hier(self, heom, M, D):
@@ -103,6 +109,21 @@ class Server:
         if key not in self._hier_cache:
             self._hier_cache[key] = heom.Hierarchy(M, D)
         return self._hier_cache[key]
+
+    def _build(self, heom, r, hier, mr, st, dev):
+        """Set up one admitted request on its stream: the run (host link records, uploads) and, when
+        it has at least one whole quantum, the CUDA graph of graph_steps steps."""
+        import torch
+
+        if dev is not None:
+            torch.cuda.set_device(dev)
+        with torch.cuda.stream(st):
+            run = heom.Run(r.prop.system, r.prop.rho0_re, r.prop.rho0_im, precision=self.precision,
+                           w=r.prop.w, max_records=mr, hier=hier, stream=st)
+            graph = None
+            if r.prop.n_steps >= self.quantum:
+                graph = heom.Batch([run], r.prop.dt_fs, self.graph_steps, self.obs_stride)
+        return run, graph
 
     def serve(self, requests, real_time: bool = True) -> ServeStats:
         """Serve `requests` (workloads.Request: arrival_s, prop, rid) and return per-request results.
@@ -120,12 +141,20 @@ class Server:
         used = 0
         streams = [torch.cuda.Stream() for _ in range(self.max_active)]
         free_streams = list(range(self.max_active))
+        dev = torch.cuda.current_device() if hasattr(torch.cuda, "current_device") else None
+        pool = ThreadPoolExecutor(self.workers) if self.workers > 0 else None
+        building: list = []  # (future, request, stream index, result)
         t0 = time.perf_counter()
 
         def now():
             return time.perf_counter() - t0
 
-        while arrivals or pending or active:
+        def activate(r, si, res, run, graph):
+            ev = torch.cuda.Event()
+            ev.record(streams[si])
+            active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph))
+
+        while arrivals or pending or active or building:
             t = now()
             while arrivals and (not real_time or arrivals[0].arrival_s <= t):
                 r = arrivals.popleft()
@@ -133,6 +162,12 @@ class Server:
                              n_steps=r.prop.n_steps)
                 results[r.rid] = res
                 s = r.prop.system
+                # a large hierarchy whose three state copies alone exceed the budget is rejected
+                # without building its tables (seconds of host time and gigabytes of host memory)
+                elem = 16 if self.precision == "fp64" else 8
+                if s.n_ado > 2_000_000 and 3 * s.n_ado * s.N * s.N * elem > self.budget:
+                    res.rejected, res.reason = True, "workspace above the device-memory budget"
+                    continue
                 hier = self._hier(heom, s.n_modes, s.D)
                 mr = (r.prop.n_steps // self.obs_stride + 2) if self.obs_stride > 0 else 2
                 try:
@@ -144,7 +179,7 @@ class Server:
                     res.rejected, res.reason = True, "workspace above the device-memory budget"
                     continue
                 pending.append((r, hier, mr))
-            # admission: first fit in arrival order
+            # admission: first fit in arrival order; the set-up runs on the worker threads
             i = 0
             while i < len(pending) and free_streams:
                 r, hier, mr = pending[i]
@@ -152,20 +187,19 @@ class Server:
                 if used + res.workspace_bytes <= self.budget:
                     del pending[i]
                     si = free_streams.pop()
-                    st = streams[si]
-                    with torch.cuda.stream(st):
-                        run = heom.Run(r.prop.system, r.prop.rho0_re, r.prop.rho0_im, precision=self.precision,
-                                       w=r.prop.w, max_records=mr, hier=hier, stream=st)
                     used += res.workspace_bytes
                     res.admitted_s = now()
-                    graph = None
-                    if r.prop.n_steps >= self.quantum:
-                        graph = heom.Batch([run], r.prop.dt_fs, self.graph_steps, self.obs_stride)
-                    ev = torch.cuda.Event()
-                    ev.record(st)
-                    active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph))
+                    if pool is None:
+                        activate(r, si, res, *self._build(heom, r, hier, mr, streams[si], None))
+                    else:
+                        building.append((pool.submit(self._build, heom, r, hier, mr, streams[si], dev), r, si, res))
                 else:
                     i += 1
+            # set-ups that finished become active
+            for b in [b for b in building if b[0].done()]:
+                building.remove(b)
+                fut, r, si, res = b
+                activate(r, si, res, *fut.result())
             # progress: finished quanta get the next quantum or complete
             progressed = False
             for a in list(active):
@@ -197,11 +231,13 @@ class Server:
                     free_streams.append(a.stream)
                     active.remove(a)
             if not progressed:
-                if arrivals and real_time and not active and not pending:
+                if arrivals and real_time and not active and not pending and not building:
                     time.sleep(max(0.0, min(arrivals[0].arrival_s - now(), 0.01)))
                 else:
                     time.sleep(0.0002)
         stats = ServeStats(results=[results[k] for k in sorted(results)], wall_s=now())
+        if pool is not None:
+            pool.shutdown(wait=True)
         return stats
 
 
@@ -217,16 +253,21 @@ def main(argv=None):
     ap.add_argument("--rates", type=float, nargs="+", default=[5, 10, 20, 50, 100, 200])
     ap.add_argument("--requests", type=int, default=500)
     ap.add_argument("--max-ado-steps", type=float, default=2e7,
-                    help="redraw requests above this ADOs x steps (a bounded sample of the mix)")
+                    help="redraw requests above this ADOs x steps (a bounded sample of the mix); 0: the full mix")
     ap.add_argument("--budget", type=float, default=120e9)
     ap.add_argument("--precision", default="fp32_mixed")
+    ap.add_argument("--workers", type=int, default=4, help="host threads that set up admitted requests")
+    ap.add_argument("--quantum", type=int, default=100)
     args = ap.parse_args(argv)
     heom.load()
+    cap = args.max_ado_steps if args.max_ado_steps > 0 else None
     for rate in args.rates:
-        reqs = wl.serving_stream(rate, args.requests, max_ado_steps=args.max_ado_steps)
-        st = Server(budget_bytes=args.budget, precision=args.precision).serve(reqs, real_time=True)
+        reqs = wl.serving_stream(rate, args.requests, max_ado_steps=cap)
+        st = Server(budget_bytes=args.budget, precision=args.precision, quantum=args.quantum,
+                    workers=args.workers).serve(reqs, real_time=True)
         s = st.summary()
-        s.update({"offered_rate_req_per_s": rate, "max_ado_steps": args.max_ado_steps, "precision": args.precision})
+        s.update({"offered_rate_req_per_s": rate, "max_ado_steps": cap, "precision": args.precision,
+                  "workers": args.workers, "rejected_fraction": s["rejected"] / max(s["requests"], 1)})
         print(json.dumps(s), flush=True)
     return 0
 
