@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/heom.h"
@@ -300,6 +301,39 @@ static int compute_modes(const heom_system *sys, std::vector<double> &gam, std::
 
 // Link records of the ADOs [u_lo, u_hi): one per valid link (up and down) and coupled state; mult[l]
 // = states of mode l's V (1 for a projector; nullptr: all 1).
+// fn(a, b) over [0, n) split into contiguous ranges, one per host thread (one thread for small n);
+// false if any range threw (host allocation).
+template <typename F>
+bool host_parallel(int64_t n, F fn) {
+  constexpr int64_t kMinPerThread = 16384;
+  const int T = (int)std::min<int64_t>(host_threads(), std::max<int64_t>(1, n / kMinPerThread));
+  std::atomic<bool> failed{false};
+  auto guarded = [&](int64_t a, int64_t b) {
+    try {
+      fn(a, b);
+    } catch (...) {
+      failed = true;
+    }
+  };
+  if (T <= 1) {
+    guarded(0, n);
+    return !failed;
+  }
+  const int64_t per = (n + T - 1) / T;
+  std::vector<std::thread> pool;
+  int64_t a = 0;
+  for (; a < n; a += per) {
+    const int64_t b = std::min(n, a + per);
+    try {
+      pool.emplace_back(guarded, a, b);
+    } catch (...) {  // no thread: this range runs here
+      guarded(a, b);
+    }
+  }
+  for (auto &th : pool) th.join();
+  return !failed;
+}
+
 int64_t count_links(const Hierarchy &h, int64_t u_lo, int64_t u_hi, const std::vector<int> *mult = nullptr) {
   int64_t k = 0;
   for (int64_t u = u_lo; u < u_hi; ++u)
@@ -533,78 +567,109 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     }
   }
 
-  // ---- per-ADO link records (CSR), decay sums
+  // ---- per-ADO link records (CSR), decay sums.  Two passes over ADO ranges on the host threads:
+  // the record count of every ADO (then prefix sums: the CSR offsets), then each ADO's records,
+  // written at its offset -- the same records in the same order as one pass in u order.
   std::vector<int64_t> loff(h.n + 1, 0);
   std::vector<double> gs(h.n, 0.0);
   std::vector<LinkRec<double>> rh;
   std::vector<LinkRec<double>> rbd;
   std::vector<LinkRec<float>> rbf;
   const bool body_fp64 = precision == HEOM_FP64;
+  const int64_t u_split = r->u_split;
+  double up_body = 0, dn_body = 0;  // valid up / down links of the body ADOs (flop accounting)
+  {
+    std::mutex acc_mu;
+    const bool ok = host_parallel(h.n, [&](int64_t a, int64_t b) {
+      double up = 0, dn = 0;
+      for (int64_t u = a; u < b; ++u) {
+        int64_t k = 0;
+        for (int l = 0; l < M; ++l) {
+          const int pv = h.plus[(size_t)u * M + l] >= 0, mv = h.minus[(size_t)u * M + l] >= 0;
+          k += (int64_t)(pv + mv) * (mp ? (*mp)[l] : 1);
+          if (u >= u_split) {
+            up += pv;
+            dn += mv;
+          }
+        }
+        loff[u + 1] = k;
+      }
+      std::lock_guard<std::mutex> lock(acc_mu);
+      up_body += up;
+      dn_body += dn;
+    });
+    if (!ok) {
+      delete r;
+      set_error("host allocation failed (link records)");
+      return HEOM_E_NOMEM;
+    }
+  }
+  for (int64_t u = 0; u < h.n; ++u) loff[u + 1] += loff[u];
+  const int64_t nlink = loff[h.n];
+  r->n_links = nlink;
+  r->rec_split = loff[u_split];
   try {
-    const int64_t lh = count_links(h, 0, r->u_split, mp);
-    const int64_t lt = mp ? count_links(h, 0, h.n, mp) : h.n_links;
-    rh.reserve(lh);
-    if (body_fp64) rbd.reserve(lt - lh);
-    else rbf.reserve(lt - lh);
+    rh.resize(r->rec_split);
+    if (body_fp64) rbd.resize(nlink - r->rec_split);
+    else rbf.resize(nlink - r->rec_split);
   } catch (...) {
     delete r;
     set_error("host allocation failed (link records)");
     return HEOM_E_NOMEM;
   }
-  int64_t nlink = 0;
   struct Pending {
     int v, s;
     double re, im;
   };
-  std::vector<Pending> pend;
-  pend.reserve(2 * (size_t)M);
-  for (int64_t u = 0; u < h.n; ++u) {
-    loff[u] = nlink;
-    double g = 0;
-    for (int l = 0; l < M; ++l) g += h.tuples[(size_t)u * M + l] * gam[l];
-    gs[u] = g;
-    pend.clear();
-    for (int l = 0; l < M; ++l) {
-      const int nl = h.tuples[(size_t)u * M + l];
-      for (int dir = 0; dir < 2; ++dir) {
-        const int32_t v = dir ? h.minus[(size_t)u * M + l] : h.plus[(size_t)u * M + l];
-        if (v < 0) continue;
-        double re, im;
-        if (dir == 0) {  // up: R = i s+
-          re = 0.0;
-          im = sp[(size_t)l * (D + 1) + nl];
-        } else {  // down: R = s- (lamnu + i c)
-          const double f = sm[(size_t)l * (D + 1) + nl];
-          re = f * lnu[l];
-          im = f * cc[l];
-        }
-        if (!sys->bath_mask) {
-          pend.push_back(Pending{v, mstate[l], re, im});
-        } else {  // one record per state of the bath's V (same coefficient)
-          const int b = l / (K + 1);
-          for (int st = 0; st < n; ++st)
-            if (sys->bath_mask[(size_t)b * n + st]) pend.push_back(Pending{v, st, re, im});
+  const bool filled = host_parallel(h.n, [&](int64_t a, int64_t b) {
+    std::vector<Pending> pend;
+    pend.reserve(2 * (size_t)M * (mp ? (size_t)n : 1));
+    for (int64_t u = a; u < b; ++u) {
+      double g = 0;
+      for (int l = 0; l < M; ++l) g += h.tuples[(size_t)u * M + l] * gam[l];
+      gs[u] = g;
+      pend.clear();
+      for (int l = 0; l < M; ++l) {
+        const int nl = h.tuples[(size_t)u * M + l];
+        for (int dir = 0; dir < 2; ++dir) {
+          const int32_t v = dir ? h.minus[(size_t)u * M + l] : h.plus[(size_t)u * M + l];
+          if (v < 0) continue;
+          double re, im;
+          if (dir == 0) {  // up: R = i s+
+            re = 0.0;
+            im = sp[(size_t)l * (D + 1) + nl];
+          } else {  // down: R = s- (lamnu + i c)
+            const double f = sm[(size_t)l * (D + 1) + nl];
+            re = f * lnu[l];
+            im = f * cc[l];
+          }
+          if (!sys->bath_mask) {
+            pend.push_back(Pending{v, mstate[l], re, im});
+          } else {  // one record per state of the bath's V (same coefficient)
+            const int bb = l / (K + 1);
+            for (int st = 0; st < n; ++st)
+              if (sys->bath_mask[(size_t)bb * n + st]) pend.push_back(Pending{v, st, re, im});
+          }
         }
       }
-    }
-    // records of one ADO ordered by state (the kernels give all records of a state to one lane);
-    // the state field also carries u mod 32 in bits 8..12 (see LinkRec)
-    std::stable_sort(pend.begin(), pend.end(), [](const Pending &x, const Pending &y) { return x.s < y.s; });
-    const int tag = (int)(u & 31) << 8;
-    for (const Pending &q : pend) {
-      if (u < r->u_split) {
-        rh.push_back(LinkRec<double>{q.v, q.s | tag, 0, 0, q.re, q.im});
-      } else if (body_fp64) {
-        rbd.push_back(LinkRec<double>{q.v, q.s | tag, 0, 0, q.re, q.im});
-      } else {
-        rbf.push_back(LinkRec<float>{q.v, q.s | tag, (float)q.re, (float)q.im});
+      // records of one ADO ordered by state (the kernels give all records of a state to one lane);
+      // the state field also carries u mod 32 in bits 8..12 (see LinkRec)
+      std::stable_sort(pend.begin(), pend.end(), [](const Pending &x, const Pending &y) { return x.s < y.s; });
+      const int tag = (int)(u & 31) << 8;
+      int64_t k = loff[u];
+      for (const Pending &q : pend) {
+        if (u < u_split) rh[k] = LinkRec<double>{q.v, q.s | tag, 0, 0, q.re, q.im};
+        else if (body_fp64) rbd[k - r->rec_split] = LinkRec<double>{q.v, q.s | tag, 0, 0, q.re, q.im};
+        else rbf[k - r->rec_split] = LinkRec<float>{q.v, q.s | tag, (float)q.re, (float)q.im};
+        ++k;
       }
-      ++nlink;
     }
+  });
+  if (!filled) {
+    delete r;
+    set_error("host allocation failed (link records)");
+    return HEOM_E_NOMEM;
   }
-  loff[h.n] = nlink;
-  r->n_links = nlink;
-  r->rec_split = loff[r->u_split];
 
   {  // algorithmic bytes and flops of one launch of the dominant kernel (ADOs u >= u_split)
     const double E = (double)n * n;
@@ -614,12 +679,7 @@ extern "C" int heom_run_create(const heom_system *sys, const heom_hier *hh, int 
     const double tab = nb * 16.0 + nlb * (body_fp64 ? sizeof(LinkRec<double>) : sizeof(LinkRec<float>));
     r->bytes_stage_y = nb * 3.0 * E * cs + tab;
     r->bytes_stage_noy = nb * 2.0 * E * cs + tab;
-    double up = 0, dn = 0;
-    for (int64_t u = r->u_split; u < h.n; ++u)
-      for (int l = 0; l < M; ++l) {
-        up += h.plus[(size_t)u * M + l] >= 0;
-        dn += h.minus[(size_t)u * M + l] >= 0;
-      }
+    const double up = up_body, dn = dn_body;
     // the Hermitian form computes H s only (s H = (H s)^dagger): half the commutator flops
     const double comm = (r->cplx_h ? 16.0 : 8.0) * n * E;
     const double links = up * 8.0 * (n - 1) + dn * 8.0 * (2 * n - 1);

@@ -9,6 +9,9 @@
 #include "hierarchy.h"
 
 #include <algorithm>
+#include <array>
+#include <atomic>
+#include <thread>
 
 #include "../../include/heom.h"
 
@@ -24,6 +27,11 @@ int64_t binom(int a, int b) {
     if (r > ((__int128)1 << 62)) return -1;
   }
   return (int64_t)r;
+}
+
+int host_threads() {
+  const unsigned hc = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(hc == 0 ? 1u : hc, 32u));
 }
 
 int build_hierarchy(int M, int D, Hierarchy *h, std::string *err) {
@@ -57,13 +65,24 @@ int build_hierarchy(int M, int D, Hierarchy *h, std::string *err) {
     return HEOM_E_NOMEM;
   }
 
-  const int nb = M - 1;                    // number of bars
-  std::vector<int> b(std::max(nb, 1));     // bar positions, 0-based slot j-1 holds b_j
-  std::vector<int64_t> pre(M + 1), sup(M + 2), sdn(M + 2);
-  for (int L = 0; L <= D; ++L) {
-    const int64_t cnt = h->level_off[L + 1] - h->level_off[L];
-    for (int j = 0; j < nb; ++j) b[j] = j;  // rank 0: all bars first (n_M = L)
-    for (int64_t r = 0; r < cnt; ++r) {
+  const int nb = M - 1;  // number of bars
+  // Ranks [r0, r1) of level L: the tuples from their bar positions, and the +/- tables by the rank
+  // formula.  Items are independent, so ranges of a level are built on several host threads.
+  auto build_range = [&](int L, int64_t r0, int64_t r1) {
+    std::vector<int> b(std::max(nb, 1));  // bar positions, 0-based slot j-1 holds b_j
+    std::vector<int64_t> pre(M + 1), sup(M + 2), sdn(M + 2);
+    // colex unrank of r0: from the top bar down, the largest position x below the bar above with
+    // C(x, j) <= the rank left
+    int64_t rem = r0;
+    int above = L + M - 1;  // one past the largest slot
+    for (int j = nb; j >= 1; --j) {
+      int x = above - 1;
+      while (Cb(x, j) > rem) --x;
+      b[j - 1] = x;
+      rem -= Cb(x, j);
+      above = x;
+    }
+    for (int64_t r = r0; r < r1; ++r) {
       const int64_t u = h->level_off[L] + r;
       uint8_t *t = &h->tuples[(size_t)u * M];
       // tuple from bars
@@ -95,19 +114,44 @@ int build_hierarchy(int M, int D, Hierarchy *h, std::string *err) {
         }
       }
       // colex successor: raise the lowest bar that can move, reset the ones below it
-      if (nb > 0 && r + 1 < cnt) {
-        const int top = L + M - 2;  // largest slot index
+      if (nb > 0 && r + 1 < r1) {
         int j = 0;
         while (j < nb - 1 && b[j] + 1 == b[j + 1]) ++j;
-        if (j == nb - 1 && b[j] + 1 > top) break;  // unreachable: cnt bounds the loop
         ++b[j];
         for (int i = 0; i < j; ++i) b[i] = i;
       }
     }
+  };
+  // work items: ranges of at most kChunk ranks of one level
+  constexpr int64_t kChunk = 1 << 15;
+  std::vector<std::array<int64_t, 3>> items;
+  for (int L = 0; L <= D; ++L) {
+    const int64_t cnt = h->level_off[L + 1] - h->level_off[L];
+    for (int64_t r0 = 0; r0 < cnt; r0 += kChunk) items.push_back({L, r0, std::min(cnt, r0 + kChunk)});
   }
-  int64_t k = 0;
-  for (size_t i = 0; i < h->plus.size(); ++i) k += (h->plus[i] >= 0) + (h->minus[i] >= 0);
-  h->n_links = k;
+  const int nthr = (int)std::min<int64_t>((int64_t)items.size(), host_threads());
+  if (nthr <= 1) {
+    for (const auto &it : items) build_range((int)it[0], it[1], it[2]);
+  } else {
+    std::atomic<size_t> next{0};
+    std::atomic<bool> failed{false};
+    std::vector<std::thread> pool;
+    for (int i = 0; i < nthr; ++i)
+      pool.emplace_back([&] {
+        try {
+          for (size_t k = next++; k < items.size(); k = next++) build_range((int)items[k][0], items[k][1], items[k][2]);
+        } catch (...) {
+          failed = true;
+        }
+      });
+    for (auto &th : pool) th.join();
+    if (failed) {
+      *err = "heom_build_hierarchy: host allocation failed";
+      return HEOM_E_NOMEM;
+    }
+  }
+  // every ADO below depth D has all M "+" links, and "-" links pair with them one to one
+  h->n_links = 2 * (int64_t)M * h->level_off[D];
   return HEOM_OK;
 }
 

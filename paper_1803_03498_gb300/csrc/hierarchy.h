@@ -20,6 +20,9 @@ struct Hierarchy {
 // Returns 0 or a negative HEOM_E_* code with *err filled.
 int build_hierarchy(int M, int D, Hierarchy *h, std::string *err);
 
+// Host threads for the parallel loops of the builder and of run set-up (hardware threads, at most 32).
+int host_threads();
+
 // C(a, b) with overflow detection (returns -1 when above 2^62).
 int64_t binom(int a, int b);
 

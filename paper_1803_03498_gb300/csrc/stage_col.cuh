@@ -39,15 +39,25 @@ namespace heom {
 
 __host__ __device__ constexpr int col_gcd(int a, int b) { return b == 0 ? a : col_gcd(b, a % b); }
 
+// Most ADOs of C columns that one pass of 32 consecutive columns touches, over the P passes of a chunk.
+__host__ __device__ constexpr int col_ring(int C, int P) {
+  int m = 1;
+  for (int q = 0; q < P; ++q) {
+    const int t = (32 * q + 31) / C - (32 * q) / C + 1;
+    m = t > m ? t : m;
+  }
+  return m;
+}
+
 template <int N>
 struct ColShape {
   static constexpr int C = 2 * N;                  // columns per ADO (both parts)
   static constexpr int G = 32 / col_gcd(C, 32);    // ADOs per warp chunk
   static constexpr int P = C * G / 32;             // passes of 32 columns per chunk
   static constexpr int E = N * N;
-  static constexpr int RING = 3;                   // Q slots: a pass touches at most 3 ADOs for C >= 16
-  static constexpr int RB = 16;                    // link records per batch
-  static constexpr int WARPS = 4;
+  static constexpr int RING = col_ring(C, P);      // Q slots: the ADOs one pass touches (N = 14: 2)
+  static constexpr int RB = 12;                    // link records per batch and finalising ADO
+  static constexpr int WARPS = 4;                  // 4 CTAs of 4 warps per SM (128 registers, < 57 KB)
   static_assert(C >= 16 && G <= 31, "column kernel covers 8 <= N <= 16");
 };
 
@@ -125,7 +135,7 @@ __device__ __forceinline__ void col_links(const LinkRec<double> *rec, int nr, co
 }
 
 template <int N>
-__global__ void __launch_bounds__(ColShape<N>::WARPS * 32) stage_col_kernel(const __grid_constant__ StageArgs<double> a) {
+__global__ void __launch_bounds__(ColShape<N>::WARPS * 32, 4) stage_col_kernel(const __grid_constant__ StageArgs<double> a) {
   using S = ColShape<N>;
   using W = ColSmem<N>;
   constexpr int C = S::C, G = S::G, P = S::P, E = S::E, RB = S::RB;

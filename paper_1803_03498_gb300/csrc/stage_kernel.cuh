@@ -66,6 +66,60 @@ __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int byte
   for (int o = lane * 16; o < bytes; o += 32 * 16) cp_async16(d + o, s + o);
 }
 
+// L2 eviction priorities.  A stage reads its own tiles once (a stream through L2), while a row it
+// gathers from a neighbour is wanted again by the neighbour's other linked ADOs of the launch (every
+// state has two modes, K + 1 in general): own tiles go in as evict_first, gathered rows as
+// evict_last.  HEOM_L2_HINTS=0 (tuning builds) drops the hints.
+#ifndef HEOM_L2_HINTS
+#define HEOM_L2_HINTS 1
+#endif
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void cp_async16_hint(void *smem, const void *gmem, uint64_t pol) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8_hint(void *smem, const void *gmem, uint64_t pol) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "l"(pol)
+               : "memory");
+}
+// own tiles: streamed once
+__device__ __forceinline__ void warp_copy16_stream(void *dst, const void *src, int bytes, int lane) {
+#if HEOM_L2_HINTS
+  const uint64_t pol = l2_evict_first();
+  char *d = reinterpret_cast<char *>(dst);
+  const char *s = reinterpret_cast<const char *>(src);
+  for (int o = lane * 16; o < bytes; o += 32 * 16) cp_async16_hint(d + o, s + o, pol);
+#else
+  warp_copy16(dst, src, bytes, lane);
+#endif
+}
+// gathered neighbour rows: kept for the neighbour's other links
+__device__ __forceinline__ void cp_async16_keep(void *smem, const void *gmem) {
+#if HEOM_L2_HINTS
+  cp_async16_hint(smem, gmem, l2_evict_last());
+#else
+  cp_async16(smem, gmem);
+#endif
+}
+__device__ __forceinline__ void cp_async8_keep(void *smem, const void *gmem) {
+#if HEOM_L2_HINTS
+  cp_async8_hint(smem, gmem, l2_evict_last());
+#else
+  cp_async8(smem, gmem);
+#endif
+}
+
 // Launch shape and buffer sizes (measured on the LHCII-like and FMO-like hierarchies; the macros
 // exist for tuning builds).  Link records per warp and batch: RC of 2N-element slices (2 RC row-only
 // slices for Hermitian runs).
@@ -129,7 +183,7 @@ __device__ __forceinline__ void issue_tiles(const typename Cplx<CT>::type *src_r
                                             void *dst, int lane) {
   using S = StageShape<N, CT, BT>;
   using C2 = typename Cplx<CT>::type;
-  warp_copy16(dst, src_region + (int64_t)(u0 - own0) * S::EpOwn, cnt * S::EpOwn * (int)sizeof(C2), lane);
+  warp_copy16_stream(dst, src_region + (int64_t)(u0 - own0) * S::EpOwn, cnt * S::EpOwn * (int)sizeof(C2), lane);
 }
 
 // Copies W consecutive elements of neighbour v, from element e of its tile, to dst.  Elements of
@@ -143,8 +197,8 @@ __device__ __forceinline__ void gather_piece(const StageCommon &c, int v, int e,
   if (v >= c.u_split) {
     const B2 *p = reinterpret_cast<const B2 *>(c.zin.body) + (int64_t)(v - c.u_split) * S::EpBody + e;
     if constexpr (sizeof(B2) == sizeof(C2)) {
-      if constexpr (W * sizeof(C2) == 16) cp_async16(dst, p);
-      else cp_async8(dst, p);
+      if constexpr (W * sizeof(C2) == 16) cp_async16_keep(dst, p);
+      else cp_async8_keep(dst, p);
     } else {  // FP32 body read by the FP64 head kernel
 #pragma unroll
       for (int w = 0; w < W; ++w) {
@@ -158,7 +212,7 @@ __device__ __forceinline__ void gather_piece(const StageCommon &c, int v, int e,
   } else {
     const double2 *p = c.zin.head + (int64_t)v * S::E + e;
     if constexpr (sizeof(C2) == 16) {
-      cp_async16(dst, p);
+      cp_async16_keep(dst, p);
     } else {  // FP64 head read by the FP32 body kernel
 #pragma unroll
       for (int w = 0; w < W; ++w) {
