@@ -27,6 +27,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving leg keeps up to 64 request streams (plus each mixed run's head stream) busy: more
+# hardware work queues than the default 8 let their kernels run side by side (read at CUDA start-up)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "ADO-RHS evals/s (FP64 vs mixed, pop err <=1e-6)"
 UNIT = "ADO-RHS evals/s"

@@ -245,6 +245,10 @@ def main(argv=None):
     """Rate sweep of the serving loop on seeded Poisson streams (one JSON line per offered rate)."""
     import argparse
     import json
+    import os
+
+    # many request streams: more hardware work queues than the default 8 (read at CUDA start-up)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
     from . import heom
     from . import workloads as wl
