@@ -64,7 +64,7 @@ def _traffic():
 
     src = os.path.join(ROOT, "paper_1803_03498_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("stage_kernel.cuh", "propagate.cu"):  # the kernel and the driver that launches it
+    for f in ("stage_kernel.cuh", "stage_col.cuh", "propagate.cu"):  # the kernels and the driver that launches them
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
     vals = {}
@@ -249,7 +249,7 @@ def fp64_and_gate(prop, gate_steps, warmup, ws, clocks):
                         "peak_basis": basis,
                         "flops": "4 N^3 per ADO (Hermitian form: H s only, s H = (H s)^dagger) + 8 N^2 "
                                  "+ 8 (N-1) per up link + 8 (2N-1) per down link",
-                        "kernel": "stage_kernel<14,double,double>", "avg_launch_ms": avg, "schedule": sched},
+                        "kernel": "stage_col_kernel<14> (column form, FP64)", "avg_launch_ms": avg, "schedule": sched},
            "clocks": clk}
     gate = {"steps": gate_steps, "records": gate_steps + 1, "max_pop_err": pop_err, "bar": 1e-6,
             "pass": pop_err <= 1e-6,

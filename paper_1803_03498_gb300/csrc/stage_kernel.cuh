@@ -104,19 +104,6 @@ __device__ __forceinline__ void warp_copy16_stream(void *dst, const void *src, i
   warp_copy16(dst, src, bytes, lane);
 #endif
 }
-// result tiles: read back only by the next stage, after the whole launch has streamed through L2
-#ifndef HEOM_L2_STORE_HINT
-#define HEOM_L2_STORE_HINT 0
-#endif
-__device__ __forceinline__ void st_stream(float4 *p, float4 w) {
-#if HEOM_L2_HINTS && HEOM_L2_STORE_HINT
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(p), "f"(w.x), "f"(w.y), "f"(w.z),
-               "f"(w.w), "l"(l2_evict_first())
-               : "memory");
-#else
-  *p = w;
-#endif
-}
 // gathered neighbour rows: kept for the neighbour's other links
 __device__ __forceinline__ void cp_async16_keep(void *smem, const void *gmem) {
 #if HEOM_L2_HINTS
@@ -468,7 +455,7 @@ __device__ __forceinline__ void store_chunk(typename Cplx<CT>::type *out_own, co
         w.z *= chv;
         w.w *= chv;
       }
-      st_stream(d4 + t, w);
+      d4[t] = w;
     }
   } else {
     for (int t = lane; t < cnt * EPO; t += 32) {
