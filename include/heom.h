@@ -305,6 +305,27 @@ int heom_batch_launch(heom_batch *b, int64_t n_launches);
 int heom_batch_destroy(heom_batch *b);
 
 /*
+ * heom_group_propagate -- advance several runs together: run i by n_steps[i] RK4 steps of dt_fs (as
+ * heom_propagate, one observable record every obs_stride steps of each run's own step count, 0 =
+ * none), sharing kernel launches.  Small mixed-precision runs (HEOM_FP32_MIXED, the matrix layout,
+ * a real H, no laser field, at most 200,000 ADOs) of equal n_states advance in work-list launches:
+ * one launch per RK4 stage and part (FP64 head, FP32 body) covers every such run of that size, each
+ * run's stage arguments staged from its own workspace, so many small requests cost a few launches
+ * per step instead of eight each.  Other runs launch on their own, on the same stream.  Everything is
+ * enqueued on cuda_stream, ordered after work already enqueued on each run's stream, and later work
+ * on each run's stream is ordered after it; the call does not block, except that writing a run's
+ * work-list stage arguments (its first grouped call, or a new dt_fs) waits for cuda_stream.
+ * Results equal heom_propagate's bit for bit: every ADO gets the same arithmetic in the same order.
+ * A work-list launch counts in heom_run_launches of each run it covers.  The paper runs independent
+ * propagations side by side (section "Distributed memory HEOM implementation"); this shares their
+ * launches on one GPU.  Errors: HEOM_E_ARG (NULL run, a run listed twice, negative steps, dt_fs
+ * beyond a run's stability bound as in heom_propagate), HEOM_E_STATE (a run with a laser field or
+ * with kernel timing on), HEOM_E_NOMEM (records would exceed a run's max_records), HEOM_E_CUDA.
+ */
+int heom_group_propagate(heom_run *const *runs, int n_runs, double dt_fs, const int64_t *n_steps, int64_t obs_stride,
+                         void *cuda_stream);
+
+/*
  * Launch schedules and the autotuner (not in the paper, whose kernels are fixed; the choices below
  * map the same arithmetic onto the GPU differently).  A stage launch covers its ADOs in chunks of
  * floor(32 / n_states) consecutive ADOs over a persistent grid of CTAs.  A schedule fixes what the

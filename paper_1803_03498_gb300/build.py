@@ -22,9 +22,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = (["hierarchy.cpp", "heom_abi.cu", "propagate.cu", "tuner.cu", "batch.cu", "aux_kernels.cu", "heom_static.cu"]
            + [f"stage_{p}_{g}.cu" for p in ("fp64", "fp32", "head") for g in "abcd"]
            + ["stage_tc_a.cu", "stage_tc_b.cu", "vec_stage_g1.cu", "vec_stage_g2.cu", "vec_stage_g4.cu", "gen_stage.cu",
-              "stage_col.cu"])
+              "stage_col.cu", "stage_list_a.cu", "stage_list_b.cu", "stage_list_c.cu", "group.cu"])
 HEADERS = ["hierarchy.h", "heom_internal.h", "heom_run.h", "stage_kernel.cuh", "stage_tc.cuh", "vec_kernel.cuh", "gen_kernel.cuh",
-           "stage_col.cuh"]
+           "stage_col.cuh", "stage_list.cuh"]
 
 
 def _nvcc():

@@ -41,6 +41,14 @@ int launch_stage(int precision, const StageCommon &c, double ch, const double *t
   return rc;
 }
 
+int launch_stage_list(int kind, int n, const ListLaunch &L, cudaStream_t st, int sm_count) {
+  int rc = launch_stage_list_a(kind, n, L, st, sm_count);
+  if (rc == 1) rc = launch_stage_list_b(kind, n, L, st, sm_count);
+  if (rc == 1) rc = launch_stage_list_c(kind, n, L, st, sm_count);
+  if (rc == 1) set_error("work-list stage kernel: n_states not compiled");
+  return rc;
+}
+
 int launch_stage_vec(int kind, const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
                      int sm_count) {
   switch (c.cpw) {
@@ -382,7 +390,8 @@ Layout make_layout(int n, const Hierarchy &h, int u_split, int precision, int64_
   L.off_rec = o; o = al(o + (size_t)std::max<int64_t>(max_records, 1) * (n + 5) * sizeof(double));
   L.off_w = o; o = al(o + (size_t)n * sizeof(double));
   L.off_cnt = o; o = al(o + 2 * sizeof(int64_t));  // record counter, device error flag
-  L.off_desc = o; o = al(o + 8 * sizeof(VecRunDesc));  // batched column-0 stage arguments (4 stages x 2)
+  // stage arguments of grouped launches: batched column-0 (4 stages x 2 VecRunDesc) or work-list (GroupRunDesc)
+  L.off_desc = o; o = al(o + std::max(8 * sizeof(VecRunDesc), sizeof(GroupRunDesc)));
   L.head_bytes = al((size_t)u_split * E * sizeof(double2));
   L.body_bytes = al((size_t)(n_ado - u_split) * *Ep * be);
   for (int c = 0; c < copies; ++c) {

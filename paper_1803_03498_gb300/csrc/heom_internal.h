@@ -205,6 +205,34 @@ int launch_stage_gen(int kind, const StageCommon &c, StateView base2, StateView 
 int launch_stage_col(const StageCommon &c, double ch, const double *term, const double *H, cudaStream_t st,
                      int sm_count);
 
+// Work-list launches (stage_list.cuh): one launch covers the same stage of many runs of equal
+// n_states (real H).  A run's stage arguments for such launches live in its workspace.
+template <typename CT>
+struct alignas(16) GroupArgs {
+  StageCommon c;
+  CT ch;                           // Horner coefficient times h
+  CT term[kMaxStates];             // terminator Delta per state
+  CT H[kMaxStates * kMaxStates];   // Re H - h0 I, row stride kMaxStates, rad/fs
+};
+// Per run: the four Horner stages of the FP32 body and of the FP64 head (mixed precision).
+struct GroupRunDesc {
+  GroupArgs<float> body[4];
+  GroupArgs<double> head[4];
+};
+constexpr int kListMaxRuns = 256;  // runs per work-list launch (kernel-parameter space)
+struct ListLaunch {
+  const void *args[kListMaxRuns];  // GroupArgs of run i for this stage and part (device)
+  int item0[kListMaxRuns + 1];     // run i owns items [item0[i], item0[i + 1]) of cpi chunks each
+  int nruns;
+  int cpi;
+};
+// One work-list launch of runs of n states: kind 1 = mixed body (FP32), 2 = mixed head (FP64 compute,
+// FP32 body neighbours).  Returns 1 when n is not compiled in the unit.
+int launch_stage_list(int kind, int n, const ListLaunch &L, cudaStream_t st, int sm_count);
+int launch_stage_list_a(int kind, int n, const ListLaunch &L, cudaStream_t st, int sm_count);
+int launch_stage_list_b(int kind, int n, const ListLaunch &L, cudaStream_t st, int sm_count);
+int launch_stage_list_c(int kind, int n, const ListLaunch &L, cudaStream_t st, int sm_count);
+
 // precision: 0 = FP64 (compute and storage double), 1 = mixed body (float, float), 2 = mixed head
 // (compute double, body storage float).
 int launch_stage(int precision, const StageCommon &c, double ch, const double *term, const double *H,

@@ -58,8 +58,10 @@ struct heom_run {
   std::vector<double> Ht, Hit;       // H(t) of the current stage (general kernel)
   size_t copy_bytes = 0;             // bytes of one state copy (head + body, matrix layout)
   double bytes_full_y = 0, bytes_full_noy = 0, flops_full = 0;  // matrix-layout accounting
-  heom::VecRunDesc *desc_dev = nullptr;    // [8] stage arguments for batched column-0 launches
-  const void *desc_owner = nullptr;  // the batch whose stage arguments desc_dev holds
+  heom::VecRunDesc *desc_dev = nullptr;    // [8] stage arguments for batched column-0 launches, or a
+                                           // GroupRunDesc for work-list launches (heom_group_propagate)
+  const void *desc_owner = nullptr;  // the batch whose stage arguments desc_dev holds (or the work-list tag)
+  double desc_dt = 0;                // time step of the work-list stage arguments in desc_dev
   std::vector<double> term;          // per state
   double max_rate = 0;               // D * max gamma
   // device

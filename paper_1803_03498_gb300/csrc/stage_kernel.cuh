@@ -473,15 +473,20 @@ __device__ __forceinline__ void store_chunk(typename Cplx<CT>::type *out_own, co
   }
 }
 
-template <int N, typename CT, typename BT, bool CPLX>
-__global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kernel(const __grid_constant__ StageArgs<CT> a) {
+// The chunks first, first + nwarps, ... below n_chunks of one stage (chunk k = ADOs u_begin + k A ..),
+// processed by the calling warp with the per-warp buffers at smem_raw + warp * WarpSmem::total.  Args is
+// StageArgs<CT> (the kernel parameters of one launch) or GroupArgs<CT> (one run of a work-list launch,
+// staged in shared memory): H, the terminator, the Horner coefficient and the StageCommon of the stage.
+template <int N, typename CT, typename BT, bool CPLX, typename Args>
+__device__ __forceinline__ void stage_chunks(const Args &a, unsigned char *smem_raw, int first, int nwarps,
+                                             int n_chunks) {
   using S = StageShape<N, CT, BT>;
   using W = WarpSmem<N, CT, BT>;
   using C2 = typename Cplx<CT>::type;
   using R = LinkRec<CT>;
-  constexpr int A = S::A, EPO = S::EpOwn;
+  constexpr int EPO = S::EpOwn;
+  constexpr int A = S::A;
   constexpr bool kOwn = S::kOwnerLinks && !CPLX;  // complex H keeps the shared-memory link path
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const StageCommon &c = a.c;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char *wb = smem_raw + warp * W::total;
@@ -514,9 +519,6 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
   const int64_t rlim = S::kOwnHead ? c.rec_split : c.n_recs;  // records [rbase, rlim) of this region
   const int own0 = S::kOwnHead ? 0 : c.u_split;
 
-  const int n_chunks = (c.u_end - c.u_begin + A - 1) / A;
-  const int nwarps = gridDim.x * S::WARPS;
-  const int first = blockIdx.x * S::WARPS + warp;
   const int cap = c.herm ? 2 * S::RC : S::RC;  // link records per batch (slice buffer: 2 N RC elements)
   // lane a <= cnt of a chunk holds link_off[u0 + a]
   auto load_offs = [&](int chn) -> int64_t {
@@ -722,6 +724,15 @@ __global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kerne
     off_nxt = off_nx2;
   }
   cp_async_wait<0>();
+}
+
+template <int N, typename CT, typename BT, bool CPLX>
+__global__ void __launch_bounds__(StageShape<N, CT, BT>::WARPS * 32) stage_kernel(const __grid_constant__ StageArgs<CT> a) {
+  using S = StageShape<N, CT, BT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n_chunks = (a.c.u_end - a.c.u_begin + S::A - 1) / S::A;
+  stage_chunks<N, CT, BT, CPLX>(a, smem_raw, blockIdx.x * S::WARPS + (int)(threadIdx.x >> 5), gridDim.x * S::WARPS,
+                                n_chunks);
 }
 
 template <int N, typename CT, typename BT, bool CPLX>

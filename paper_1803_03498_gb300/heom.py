@@ -30,6 +30,7 @@ ABI_SYMBOLS = [
     "heom_batch_create", "heom_batch_launch", "heom_batch_destroy", "heom_bath_modes", "heom_run_layout",
     "heom_schedule_candidates", "heom_tune", "heom_set_autotune", "heom_get_schedule", "heom_set_schedule",
     "heom_tune_cache_clear", "heom_batch_schedule", "heom_set_default_schedule", "heom_run_set_field",
+    "heom_group_propagate",
 ]
 MATSUBARA, PADE = 0, 1
 DECOMPOSITIONS = {"matsubara": MATSUBARA, "pade": PADE}
@@ -116,6 +117,7 @@ def load():
     L.heom_batch_create.argtypes = [P(vp), i, d, i64, i64, P(vp)]
     L.heom_batch_launch.argtypes = [vp, i64]
     L.heom_batch_destroy.argtypes = [vp]
+    L.heom_group_propagate.argtypes = [P(vp), i, d, P(i64), i64, vp]
     L.heom_propagate_static.argtypes = [P(_System), vp, i, P(d), P(d), P(d), d, i64, i64, vp, P(d), i64, P(i64),
                                         P(d), P(d)]
     S = _Schedule
@@ -422,6 +424,23 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def group_propagate(runs, dt_fs: float, n_steps, obs_stride: int = 0, stream=None):
+    """heom_group_propagate: advance runs[i] by n_steps[i] RK4 steps (an int applies to every run),
+    small mixed-precision runs of equal size sharing work-list launches; enqueued on `stream`
+    (default: torch's current stream)."""
+    import torch
+
+    L = load()
+    runs = list(runs)
+    steps = [int(n_steps)] * len(runs) if np.isscalar(n_steps) else [int(x) for x in n_steps]
+    if len(steps) != len(runs):
+        raise ValueError("one step count per run")
+    arr = (ctypes.c_void_p * len(runs))(*[r._r.value for r in runs])
+    st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    sarr = (ctypes.c_int64 * len(runs))(*steps)
+    _check(L.heom_group_propagate(arr, len(runs), float(dt_fs), sarr, int(obs_stride), ctypes.c_void_p(st)))
 
 
 def propagate_static(system, rho0_re, rho0_im=None, precision="fp64", w=None, dt_fs=1.0, n_steps=0, obs_stride=1,

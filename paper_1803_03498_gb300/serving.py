@@ -7,10 +7,15 @@ A request is one propagation (system, rho(0), dt, steps).  The server
   * builds each admitted request's run (link records on the host, uploads, the CUDA graph) on a pool
     of `workers` host threads -- the library releases the interpreter lock, so several runs are set
     up at once while the main loop keeps launching;
-  * gives every admitted request its own CUDA stream and advances it by `quantum` RK4 steps at a time
-    (replays of a CUDA graph of `graph_steps` steps captured at admission, by default the whole
-    quantum: one launch on the host per quantum), so
-    the work of all admitted requests overlaps on the device, and requests that arrive while others
+  * batches the RK4 steps of the small requests (mixed precision, at most `group_max_ados` ADOs): in
+    each tick every admitted small request advances by up to `quantum` steps in one
+    heom_group_propagate call, where the runs of equal n_states share one work-list launch per stage
+    and part -- a few launches per step for all of them instead of eight per request; requests
+    admitted during a tick join the next one;
+  * gives every larger admitted request its own CUDA stream and advances it by `quantum` RK4 steps at
+    a time (replays of a CUDA graph of `graph_steps` steps captured at admission, by default the whole
+    quantum: one launch on the host per quantum), beside the ticks;
+    so the work of all admitted requests overlaps on the device, and requests that arrive while others
     are running are admitted as soon as memory frees up (no batch boundary: continuous batching);
   * on completion copies the observables back, frees the workspace and records the latency
     (completion - arrival, wall clock).
@@ -57,6 +62,7 @@ class _Active:
     result: Result
     nbytes: int
     graph: object = None
+    small: bool = False  # advanced in the batched ticks (heom_group_propagate)
 
 
 @dataclass
@@ -87,7 +93,7 @@ class ServeStats:
 class Server:
     def __init__(self, budget_bytes: float = 120e9, precision: str = "fp32_mixed", quantum: int = 100,
                  max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False, graph_steps: int | None = None,
-                 workers: int = 4):
+                 workers: int = 4, group_max_ados: int = 200000):
         if obs_stride > 0 and quantum % obs_stride:
             raise ValueError("obs_stride must divide quantum")
         if graph_steps is None:  # one graph per quantum (measured: fewer, longer graphs serve more)
@@ -102,6 +108,8 @@ class Server:
         self.keep_sigma0 = keep_sigma0
         self.graph_steps = int(graph_steps)
         self.workers = max(0, int(workers))
+        # requests up to this many ADOs (mixed precision) advance in the batched ticks; 0: none
+        self.group_max_ados = int(group_max_ados) if precision == "fp32_mixed" else 0
         self._hier_cache = {}
 
     def _hier(self, heom, M, D):
@@ -110,9 +118,12 @@ class Server:
             self._hier_cache[key] = heom.Hierarchy(M, D)
         return self._hier_cache[key]
 
+    def _small(self, r) -> bool:
+        return r.prop.system.n_ado <= self.group_max_ados
+
     def _build(self, heom, r, hier, mr, st, dev):
-        """Set up one admitted request on its stream: the run (host link records, uploads) and, when
-        it has at least one whole quantum, the CUDA graph of graph_steps steps."""
+        """Set up one admitted request on its stream: the run (host link records, uploads) and, for a
+        larger request with at least one whole quantum, the CUDA graph of graph_steps steps."""
         import torch
 
         if dev is not None:
@@ -121,7 +132,7 @@ class Server:
             run = heom.Run(r.prop.system, r.prop.rho0_re, r.prop.rho0_im, precision=self.precision,
                            w=r.prop.w, max_records=mr, hier=hier, stream=st)
             graph = None
-            if r.prop.n_steps >= self.quantum:
+            if r.prop.n_steps >= self.quantum and not self._small(r):
                 graph = heom.Batch([run], r.prop.dt_fs, self.graph_steps, self.obs_stride)
         return run, graph
 
@@ -152,9 +163,27 @@ class Server:
         def activate(r, si, res, run, graph):
             ev = torch.cuda.Event()
             ev.record(streams[si])
-            active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph))
+            active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph, self._small(r)))
 
-        while arrivals or pending or active or building:
+        def complete(a):
+            nonlocal used
+            res = a.result
+            res.observables = a.run.observables()
+            if self.keep_sigma0:
+                res.sigma0 = a.run.sigma0()
+            res.done_s = now()
+            if a.graph is not None:
+                a.graph.close()
+            a.run.close()
+            a.run = None
+            used -= a.nbytes
+            free_streams.append(a.stream)
+            active.remove(a)
+
+        group_stream = torch.cuda.Stream() if self.group_max_ados > 0 else None
+        tick = None  # event of the batched tick in flight
+
+        while arrivals or pending or active or building or tick is not None:
             t = now()
             while arrivals and (not real_time or arrivals[0].arrival_s <= t):
                 r = arrivals.popleft()
@@ -200,10 +229,31 @@ class Server:
                 building.remove(b)
                 fut, r, si, res = b
                 activate(r, si, res, *fut.result())
-            # progress: finished quanta get the next quantum or complete
+            # batched tick of the small requests: when the previous one is done, finished requests
+            # complete and every other small request advances by up to a quantum in one call
             progressed = False
+            if group_stream is not None and (tick is None or tick.query()):
+                tick = None
+                small = [a for a in active if a.small]
+                for a in [a for a in small if a.remaining == 0]:
+                    complete(a)
+                    progressed = True
+                by_dt = {}
+                for a in small:
+                    if a.remaining > 0:
+                        by_dt.setdefault(a.req.prop.dt_fs, []).append(a)
+                for dt, members in by_dt.items():
+                    steps = [min(self.quantum, a.remaining) for a in members]
+                    heom.group_propagate([a.run for a in members], dt, steps, self.obs_stride, stream=group_stream)
+                    for a, q in zip(members, steps):
+                        a.remaining -= q
+                if by_dt:
+                    tick = torch.cuda.Event()
+                    tick.record(group_stream)
+                    progressed = True
+            # progress of the larger requests: finished quanta get the next quantum or complete
             for a in list(active):
-                if not a.event.query():
+                if a.small or not a.event.query():
                     continue
                 progressed = True
                 if a.remaining > 0:
@@ -218,18 +268,7 @@ class Server:
                     a.event = torch.cuda.Event()
                     a.event.record(st)
                 else:
-                    res = a.result
-                    res.observables = a.run.observables()
-                    if self.keep_sigma0:
-                        res.sigma0 = a.run.sigma0()
-                    res.done_s = now()
-                    if a.graph is not None:
-                        a.graph.close()
-                    a.run.close()
-                    a.run = None
-                    used -= a.nbytes
-                    free_streams.append(a.stream)
-                    active.remove(a)
+                    complete(a)
             if not progressed:
                 if arrivals and real_time and not active and not pending and not building:
                     time.sleep(max(0.0, min(arrivals[0].arrival_s - now(), 0.01)))

@@ -19,6 +19,8 @@ class FakeState:
         self.created = []
         self.graph_launches = {}
         self.tails = {}
+        self.ticks = []
+        self.grouped = {}
 
 
 def fake_modules(state, sizes):
@@ -68,6 +70,13 @@ def fake_modules(state, sizes):
     heom.Run = Run
     heom.Batch = Batch
 
+    def group_propagate(runs, dt, steps, obs_stride=0, stream=None):
+        state.ticks.append({r.name: q for r, q in zip(runs, steps)})
+        for r, q in zip(runs, steps):
+            state.grouped[r.name] = state.grouped.get(r.name, 0) + q
+
+    heom.group_propagate = group_propagate
+
     class Stream:
         pass
 
@@ -114,7 +123,8 @@ def test_admission_budget_quanta_and_release(monkeypatch, workers):
     monkeypatch.setitem(__import__("sys").modules, "paper_1803_03498_gb300.heom", heom)
     monkeypatch.setattr(torch, "cuda", cuda)
     reqs = make_requests([("a", 250), ("b", 100), ("huge", 100), ("c", 40), ("d", 320)])
-    stats = serving.Server(budget_bytes=100, quantum=100, max_active=3, workers=workers).serve(reqs, real_time=False)
+    stats = serving.Server(budget_bytes=100, quantum=100, max_active=3, workers=workers,
+                           group_max_ados=0).serve(reqs, real_time=False)
     res = {r.rid: r for r in stats.results}
     # the request larger than the whole budget is rejected at arrival, the rest complete
     assert res[2].rejected and "budget" in res[2].reason
@@ -138,3 +148,28 @@ def test_server_argument_checks():
         serving.Server(quantum=100, obs_stride=30)
     with pytest.raises(ValueError):
         serving.Server(quantum=100, graph_steps=30)
+
+
+@pytest.mark.parametrize("workers", [0, 2])
+def test_small_requests_advance_in_batched_ticks(monkeypatch, workers):
+    """Small requests advance together: each tick advances every admitted small request by up to a
+    quantum in one group call; a request finishes after exactly its steps; memory is released."""
+    import torch
+
+    import paper_1803_03498_gb300 as pkg
+
+    state = FakeState()
+    sizes = {"a": 10, "b": 10, "c": 10, "d": 10}
+    heom, cuda = fake_modules(state, sizes)
+    monkeypatch.setattr(pkg, "heom", heom, raising=False)
+    monkeypatch.setitem(__import__("sys").modules, "paper_1803_03498_gb300.heom", heom)
+    monkeypatch.setattr(torch, "cuda", cuda)
+    reqs = make_requests([("a", 250), ("b", 100), ("c", 40), ("d", 0)])
+    stats = serving.Server(budget_bytes=100, quantum=100, max_active=4, workers=workers).serve(reqs, real_time=False)
+    assert all(not r.rejected and np.isfinite(r.done_s) for r in stats.results)
+    assert state.grouped == {"a": 250, "b": 100, "c": 40}
+    assert state.graph_launches == {} and all(v == 0 for v in state.tails.values())
+    # no tick advances a request by more than a quantum, and the first tick covers everything admitted
+    assert all(q <= 100 for t in state.ticks for q in t.values())
+    assert max(len(t) for t in state.ticks) >= 2
+    assert state.used == 0
