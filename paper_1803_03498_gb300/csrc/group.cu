@@ -20,8 +20,11 @@ namespace {
 // Runs above this many body ADOs keep launches of their own: the work-list kernel reads H from
 // shared memory instead of the constant bank, which costs at the sizes where one run fills the GPU.
 constexpr int64_t kListRunMaxAdos = 200000;
-constexpr int kListCpiBody = 16;  // chunks per work item: 4 per warp of the 4-warp FP32 kernel
-constexpr int kListCpiHead = 8;   // 4 per warp of the 2-warp FP64 head kernel
+// Chunks per work item: one per warp (4-warp FP32 body kernel, 2-warp FP64 head kernel), so that a
+// small run spreads over as many CTAs as it has chunks -- at these sizes a launch is latency-bound,
+// and the FP64 head of a large n_states (one ADO per chunk) is the longest chain.
+constexpr int kListCpiBody = 4;
+constexpr int kListCpiHead = 2;
 const char kListTag = 0;          // desc_owner of runs whose descriptor area holds work-list arguments
 
 // The Horner stages of one RK4 step: (input, base, output, coefficient of h).
@@ -156,10 +159,31 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
   }
 
   int rc = HEOM_OK;
+  // Each size class gets a stream of its own for the whole call (forked from and joined back into the
+  // caller's stream): the classes' launch chains run side by side, while the stages of one class
+  // follow each other.  A run keeps its class, so its launches stay in order.
+  std::vector<cudaStream_t> cls(kMaxStates + 1, nullptr);
+  std::vector<cudaEvent_t> cls_ev;
+  auto class_stream = [&](int n) -> cudaStream_t {
+    if (!cls[n]) {
+      cudaEvent_t fe = nullptr;
+      cudaError_t ce = cudaStreamCreateWithFlags(&cls[n], cudaStreamNonBlocking);
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&fe, cudaEventDisableTiming);
+      if (ce == cudaSuccess) cls_ev.push_back(fe);
+      if (ce == cudaSuccess) ce = cudaEventRecord(fe, gs);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cls[n], fe, 0);
+      if (ce != cudaSuccess) {
+        cuda_fail("heom_group_propagate: class stream", ce);
+        return nullptr;
+      }
+    }
+    return cls[n];
+  };
   // the work-list launches of one step, rebuilt only when a run's steps end: per class of equal
   // n_states and per batch of at most kListMaxRuns runs, the head and body launch of each stage
   struct Prepared {
     int n, kind, sm_count;
+    cudaStream_t stream;
     ListLaunch L[4];
     std::vector<heom_run *> members;
   };
@@ -173,7 +197,12 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
       for (int i = 0; i < n_runs; ++i)
         if (listed[i] && n_steps[i] > s) classes[rv[i]->n].push_back(i);
       prep.clear();
-      for (const auto &cl : classes)
+      for (const auto &cl : classes) {
+        cudaStream_t cs = class_stream(cl.first);
+        if (!cs) {
+          rc = HEOM_E_CUDA;
+          break;
+        }
         for (size_t b0 = 0; b0 < cl.second.size(); b0 += kListMaxRuns) {
           const size_t b1 = std::min(cl.second.size(), b0 + (size_t)kListMaxRuns);
           for (int part = 0; part < 2; ++part) {  // FP64 head, then FP32 body
@@ -181,6 +210,7 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
             p.n = cl.first;
             p.kind = part == 0 ? 2 : 1;
             p.sm_count = rv[cl.second[b0]]->sm_count;
+            p.stream = cs;
             for (int st = 0; st < 4; ++st) {
               ListLaunch &L = p.L[st];
               L.nruns = (int)(b1 - b0);
@@ -200,17 +230,18 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
             prep.push_back(std::move(p));
           }
         }
+      }
       rebuilt_at = s;
     }
     for (int st = 0; st < 4 && rc == HEOM_OK; ++st) {
       for (Prepared &p : prep) {
-        if (launch_stage_list(p.kind, p.n, p.L[st], gs, p.sm_count)) {
+        if (launch_stage_list(p.kind, p.n, p.L[st], p.stream, p.sm_count)) {
           rc = HEOM_E_CUDA;
           break;
         }
         for (heom_run *r : p.members) ++r->launches;  // one work-list launch counts for each of its runs
       }
-      // runs outside the work lists: their own launches, on the group stream
+      // runs outside the work lists: their own launches, on the caller's stream
       for (int i = 0; i < n_runs && rc == HEOM_OK; ++i) {
         if (listed[i] || n_steps[i] <= s) continue;
         heom_run *r = rv[i];
@@ -228,12 +259,24 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
       r->t_fs += h;
       if (obs_stride > 0 && r->steps_done % obs_stride == 0) {
         cudaStream_t own = r->stream;
-        r->stream = gs;
+        r->stream = listed[i] ? cls[r->n] : gs;  // after the run's own stage launches
         rc = enqueue_record(r);
         r->stream = own;
       }
     }
   }
+  // join the class streams back into the caller's stream
+  for (int n = 0; n <= kMaxStates; ++n) {
+    if (!cls[n]) continue;
+    cudaEvent_t je = nullptr;
+    cudaError_t ce = cudaEventCreateWithFlags(&je, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventRecord(je, cls[n]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(gs, je, 0);
+    if (je) cudaEventDestroy(je);
+    cudaStreamDestroy(cls[n]);  // released once its work is done
+    if (ce != cudaSuccess && rc == HEOM_OK) rc = cuda_fail("heom_group_propagate: class stream join", ce);
+  }
+  for (cudaEvent_t fe : cls_ev) cudaEventDestroy(fe);
 
   // later work on every run's stream is ordered after this call's launches
   e = cudaEventRecord(evs.back(), gs);

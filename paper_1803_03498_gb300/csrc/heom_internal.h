@@ -219,7 +219,7 @@ struct GroupRunDesc {
   GroupArgs<float> body[4];
   GroupArgs<double> head[4];
 };
-constexpr int kListMaxRuns = 256;  // runs per work-list launch (kernel-parameter space)
+constexpr int kListMaxRuns = 64;  // runs per work-list launch (kernel parameters: about 0.8 KB)
 struct ListLaunch {
   const void *args[kListMaxRuns];  // GroupArgs of run i for this stage and part (device)
   int item0[kListMaxRuns + 1];     // run i owns items [item0[i], item0[i + 1]) of cpi chunks each

@@ -75,7 +75,7 @@ def test_group_equals_one_by_one(heom):
 
 
 def test_more_runs_of_one_size_than_one_launch_holds(heom):
-    """300 dimers of different couplings (256 per launch at most): each equals its own propagation."""
+    """300 dimers of different couplings (64 per launch at most): each equals its own propagation."""
     rng = np.random.default_rng(1803201)
     props = []
     for k in range(300):
