@@ -301,16 +301,18 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32_mixed")
     ap.add_argument("--workers", type=int, default=4, help="host threads that set up admitted requests")
     ap.add_argument("--quantum", type=int, default=100)
+    ap.add_argument("--max-active", type=int, default=64, help="requests admitted at once (streams)")
     args = ap.parse_args(argv)
     heom.load()
     cap = args.max_ado_steps if args.max_ado_steps > 0 else None
     for rate in args.rates:
         reqs = wl.serving_stream(rate, args.requests, max_ado_steps=cap)
         st = Server(budget_bytes=args.budget, precision=args.precision, quantum=args.quantum,
-                    workers=args.workers).serve(reqs, real_time=True)
+                    workers=args.workers, max_active=args.max_active).serve(reqs, real_time=True)
         s = st.summary()
         s.update({"offered_rate_req_per_s": rate, "max_ado_steps": cap, "precision": args.precision,
-                  "workers": args.workers, "rejected_fraction": s["rejected"] / max(s["requests"], 1)})
+                  "workers": args.workers, "max_active": args.max_active, "quantum": args.quantum,
+                  "rejected_fraction": s["rejected"] / max(s["requests"], 1)})
         print(json.dumps(s), flush=True)
     return 0
 
