@@ -164,7 +164,16 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
   // follow each other.  A run keeps its class, so its launches stay in order.
   std::vector<cudaStream_t> cls(kMaxStates + 1, nullptr);
   std::vector<cudaEvent_t> cls_ev;
+  // one size class and nothing else: its launches go straight to the caller's stream
+  bool single = true;
+  int n0 = -1;
+  for (int i = 0; i < n_runs && single; ++i) {
+    if (n_steps[i] == 0) continue;
+    if (n0 < 0) n0 = rv[i]->n;
+    single = listed[i] && rv[i]->n == n0;
+  }
   auto class_stream = [&](int n) -> cudaStream_t {
+    if (single) return gs;
     if (!cls[n]) {
       cudaEvent_t fe = nullptr;
       cudaError_t ce = cudaStreamCreateWithFlags(&cls[n], cudaStreamNonBlocking);
@@ -259,7 +268,7 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
       r->t_fs += h;
       if (obs_stride > 0 && r->steps_done % obs_stride == 0) {
         cudaStream_t own = r->stream;
-        r->stream = listed[i] ? cls[r->n] : gs;  // after the run's own stage launches
+        r->stream = (listed[i] && !single) ? cls[r->n] : gs;  // after the run's own stage launches
         rc = enqueue_record(r);
         r->stream = own;
       }

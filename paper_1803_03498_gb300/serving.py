@@ -239,7 +239,9 @@ class Server:
                     if a.small:
                         classes.setdefault((a.req.prop.dt_fs, a.req.prop.system.N), []).append(a)
                 for key, members in classes.items():
-                    t = ticks.setdefault(key, [torch.cuda.Stream(), None])
+                    if key not in ticks:
+                        ticks[key] = [torch.cuda.Stream(), None]
+                    t = ticks[key]
                     if t[1] is not None and not t[1].query():
                         continue
                     t[1] = None
