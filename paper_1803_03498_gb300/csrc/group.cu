@@ -172,8 +172,11 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
     if (n0 < 0) n0 = rv[i]->n;
     single = listed[i] && rv[i]->n == n0;
   }
-  auto class_stream = [&](int n) -> cudaStream_t {
-    if (single) return gs;
+  // the stream of size class n in *out (the caller's stream, which may be the NULL stream, when the call
+  // has a single class)
+  auto class_stream = [&](int n, cudaStream_t *out) -> int {
+    *out = gs;
+    if (single) return HEOM_OK;
     if (!cls[n]) {
       cudaEvent_t fe = nullptr;
       cudaError_t ce = cudaStreamCreateWithFlags(&cls[n], cudaStreamNonBlocking);
@@ -181,12 +184,10 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
       if (ce == cudaSuccess) cls_ev.push_back(fe);
       if (ce == cudaSuccess) ce = cudaEventRecord(fe, gs);
       if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cls[n], fe, 0);
-      if (ce != cudaSuccess) {
-        cuda_fail("heom_group_propagate: class stream", ce);
-        return nullptr;
-      }
+      if (ce != cudaSuccess) return cuda_fail("heom_group_propagate: class stream", ce);
     }
-    return cls[n];
+    *out = cls[n];
+    return HEOM_OK;
   };
   // the work-list launches of one step, rebuilt only when a run's steps end: per class of equal
   // n_states and per batch of at most kListMaxRuns runs, the head and body launch of each stage
@@ -207,11 +208,8 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
         if (listed[i] && n_steps[i] > s) classes[rv[i]->n].push_back(i);
       prep.clear();
       for (const auto &cl : classes) {
-        cudaStream_t cs = class_stream(cl.first);
-        if (!cs) {
-          rc = HEOM_E_CUDA;
-          break;
-        }
+        cudaStream_t cs = gs;
+        if ((rc = class_stream(cl.first, &cs)) != HEOM_OK) break;
         for (size_t b0 = 0; b0 < cl.second.size(); b0 += kListMaxRuns) {
           const size_t b1 = std::min(cl.second.size(), b0 + (size_t)kListMaxRuns);
           for (int part = 0; part < 2; ++part) {  // FP64 head, then FP32 body
