@@ -7,12 +7,11 @@ A request is one propagation (system, rho(0), dt, steps).  The server
   * builds each admitted request's run (link records on the host, uploads, the CUDA graph) on a pool
     of `workers` host threads -- the library releases the interpreter lock, so several runs are set
     up at once while the main loop keeps launching;
-  * batches the RK4 steps of the small requests (mixed precision, at most `group_max_ados` ADOs) of
-    equal n_states (and time step): in each tick of such a class every admitted member advances by up
-    to `quantum` steps in one heom_group_propagate call, where they share one work-list launch per
-    stage and part -- eight launches per step for the whole class instead of eight per request; the
-    classes tick independently (a class of large runs does not hold up the others), on their own
-    streams, and requests admitted during a tick join their class's next one;
+  * batches the RK4 steps of the small requests (mixed precision, at most `group_max_ados` ADOs): in
+    each tick every admitted small request advances by up to `quantum` steps in one
+    heom_group_propagate call, where the runs of equal n_states share one work-list launch per stage
+    and part -- a few launches per step for all of them instead of eight per request; requests
+    admitted during a tick join the next one;
   * gives every larger admitted request its own CUDA stream and advances it by `quantum` RK4 steps at
     a time (replays of a CUDA graph of `graph_steps` steps captured at admission, by default the whole
     quantum: one launch on the host per quantum), beside the ticks;
@@ -181,10 +180,10 @@ class Server:
             free_streams.append(a.stream)
             active.remove(a)
 
-        grouped = self.group_max_ados > 0
-        ticks = {}  # (dt, n_states) -> [stream, event of the tick in flight or None]
+        group_stream = torch.cuda.Stream() if self.group_max_ados > 0 else None
+        tick = None  # event of the batched tick in flight
 
-        while arrivals or pending or active or building:
+        while arrivals or pending or active or building or tick is not None:
             t = now()
             while arrivals and (not real_time or arrivals[0].arrival_s <= t):
                 r = arrivals.popleft()
@@ -233,30 +232,24 @@ class Server:
             # batched tick of the small requests: when the previous one is done, finished requests
             # complete and every other small request advances by up to a quantum in one call
             progressed = False
-            if grouped:
-                classes = {}
-                for a in active:
-                    if a.small:
-                        classes.setdefault((a.req.prop.dt_fs, a.req.prop.system.N), []).append(a)
-                for key, members in classes.items():
-                    if key not in ticks:
-                        ticks[key] = [torch.cuda.Stream(), None]
-                    t = ticks[key]
-                    if t[1] is not None and not t[1].query():
-                        continue
-                    t[1] = None
-                    for a in [a for a in members if a.remaining == 0]:
-                        complete(a)
-                        progressed = True
-                    members = [a for a in members if a.remaining > 0]
-                    if not members:
-                        continue
+            if group_stream is not None and (tick is None or tick.query()):
+                tick = None
+                small = [a for a in active if a.small]
+                for a in [a for a in small if a.remaining == 0]:
+                    complete(a)
+                    progressed = True
+                by_dt = {}
+                for a in small:
+                    if a.remaining > 0:
+                        by_dt.setdefault(a.req.prop.dt_fs, []).append(a)
+                for dt, members in by_dt.items():
                     steps = [min(self.quantum, a.remaining) for a in members]
-                    heom.group_propagate([a.run for a in members], key[0], steps, self.obs_stride, stream=t[0])
+                    heom.group_propagate([a.run for a in members], dt, steps, self.obs_stride, stream=group_stream)
                     for a, q in zip(members, steps):
                         a.remaining -= q
-                    t[1] = torch.cuda.Event()
-                    t[1].record(t[0])
+                if by_dt:
+                    tick = torch.cuda.Event()
+                    tick.record(group_stream)
                     progressed = True
             # progress of the larger requests: finished quanta get the next quantum or complete
             for a in list(active):
@@ -308,7 +301,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32_mixed")
     ap.add_argument("--workers", type=int, default=4, help="host threads that set up admitted requests")
     ap.add_argument("--quantum", type=int, default=100)
-    ap.add_argument("--max-active", type=int, default=64, help="requests admitted at once (streams)")
+    ap.add_argument("--max-active", type=int, default=256, help="requests admitted at once (streams)")
     args = ap.parse_args(argv)
     heom.load()
     cap = args.max_ado_steps if args.max_ado_steps > 0 else None
