@@ -159,7 +159,7 @@ struct StageArgs {
   StageCommon c;
   CT ch;                      // Horner coefficient times h (1 for a bare RHS evaluation)
   CT term[kMaxStates];        // terminator Delta per state (0 if none)
-  CT H[kMaxStates * kMaxStates];   // Re H - h0 I, row stride kMaxStates, rad/fs
+  alignas(16) CT H[kMaxStates * kMaxStates];   // Re H - h0 I, row stride kMaxStates, rad/fs (pairs load as 8 bytes)
   CT Hi[kMaxStates * kMaxStates];  // Im H
 };
 
@@ -212,7 +212,7 @@ struct alignas(16) GroupArgs {
   StageCommon c;
   CT ch;                           // Horner coefficient times h
   CT term[kMaxStates];             // terminator Delta per state
-  CT H[kMaxStates * kMaxStates];   // Re H - h0 I, row stride kMaxStates, rad/fs
+  alignas(16) CT H[kMaxStates * kMaxStates];   // Re H - h0 I, row stride kMaxStates, rad/fs
 };
 // Per run: the four Horner stages of the FP32 body and of the FP64 head (mixed precision).
 struct GroupRunDesc {

@@ -120,6 +120,26 @@ __device__ __forceinline__ void cp_async8_keep(void *smem, const void *gmem) {
 #endif
 }
 
+// Packed FP32x2 FMA (sm_100 family): two independent fma.rn.f32 in one instruction, so the same
+// results as two scalar FMAs with half the issue slots.  HEOM_FFMA2=0 (tuning builds) keeps scalar FMAs.
+#ifndef HEOM_FFMA2
+#define HEOM_FFMA2 1
+#endif
+constexpr bool kFfma2 = HEOM_FFMA2 != 0;
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Launch shape and buffer sizes (measured on the LHCII-like and FMO-like hierarchies; the macros
 // exist for tuning builds).  Link records per warp and batch: RC of 2N-element slices (2 RC row-only
 // slices for Hermitian runs).
@@ -621,14 +641,40 @@ __device__ __forceinline__ void stage_chunks(const Args &a, unsigned char *smem_
           }
         }
         if (!herm || own_path) {  // + i (s H); on the owner path Q = i S with S = s H from the own row
+          if constexpr (kFfma2 && sizeof(CT) == 4 && N % 2 == 0) {
+            // the same FMAs, two columns per packed FP32x2 instruction (bit-identical results)
+            uint64_t pr[N / 2], pi[N / 2];
 #pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const C2 zk = zr[k];
+            for (int jp = 0; jp < N / 2; ++jp) {
+              pr[jp] = pack2(rr[2 * jp], rr[2 * jp + 1]);
+              pi[jp] = pack2(ri[2 * jp], ri[2 * jp + 1]);
+            }
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-              const CT h = a.H[k * kMaxStates + j];
-              rr[j] = fma(-zk.y, h, rr[j]);
-              ri[j] = fma(zk.x, h, ri[j]);
+            for (int k = 0; k < N; ++k) {
+              const C2 zk = zr[k];
+              const uint64_t sy = pack2(-zk.y, -zk.y), sx = pack2(zk.x, zk.x);
+#pragma unroll
+              for (int jp = 0; jp < N / 2; ++jp) {
+                const uint64_t hp = *reinterpret_cast<const uint64_t *>(&a.H[k * kMaxStates + 2 * jp]);
+                pr[jp] = ffma2(sy, hp, pr[jp]);
+                pi[jp] = ffma2(sx, hp, pi[jp]);
+              }
+            }
+#pragma unroll
+            for (int jp = 0; jp < N / 2; ++jp) {
+              unpack2(pr[jp], rr[2 * jp], rr[2 * jp + 1]);
+              unpack2(pi[jp], ri[2 * jp], ri[2 * jp + 1]);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              const C2 zk = zr[k];
+#pragma unroll
+              for (int j = 0; j < N; ++j) {
+                const CT h = a.H[k * kMaxStates + j];
+                rr[j] = fma(-zk.y, h, rr[j]);
+                ri[j] = fma(zk.x, h, ri[j]);
+              }
             }
           }
           if constexpr (CPLX) {
