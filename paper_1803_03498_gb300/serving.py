@@ -93,7 +93,7 @@ class ServeStats:
 class Server:
     def __init__(self, budget_bytes: float = 120e9, precision: str = "fp32_mixed", quantum: int = 100,
                  max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False, graph_steps: int | None = None,
-                 workers: int = 4, group_max_ados: int = 200000):
+                 workers: int = 4, group_max_ados: int = 200000, large_occupancy_pct: int = 50):
         if obs_stride > 0 and quantum % obs_stride:
             raise ValueError("obs_stride must divide quantum")
         if graph_steps is None:  # one graph per quantum (measured: fewer, longer graphs serve more)
@@ -110,6 +110,9 @@ class Server:
         self.workers = max(0, int(workers))
         # requests up to this many ADOs (mixed precision) advance in the batched ticks; 0: none
         self.group_max_ados = int(group_max_ados) if precision == "fp32_mixed" else 0
+        # a larger request's persistent stage kernels fill only this share of each SM's CTA slots, so
+        # that the small requests' launches find free SMs instead of waiting for whole launches of it
+        self.large_occupancy_pct = int(large_occupancy_pct)
         self._hier_cache = {}
 
     def _hier(self, heom, M, D):
@@ -131,6 +134,8 @@ class Server:
         with torch.cuda.stream(st):
             run = heom.Run(r.prop.system, r.prop.rho0_re, r.prop.rho0_im, precision=self.precision,
                            w=r.prop.w, max_records=mr, hier=hier, stream=st)
+            if not self._small(r) and 0 < self.large_occupancy_pct < 100:
+                run.set_schedule(self.large_occupancy_pct, 1, part=0)
             graph = None
             if r.prop.n_steps >= self.quantum and not self._small(r):
                 graph = heom.Batch([run], r.prop.dt_fs, self.graph_steps, self.obs_stride)

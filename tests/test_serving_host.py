@@ -21,6 +21,7 @@ class FakeState:
         self.tails = {}
         self.ticks = []
         self.grouped = {}
+        self.schedules = {}
 
 
 def fake_modules(state, sizes):
@@ -45,6 +46,9 @@ def fake_modules(state, sizes):
 
         def propagate(self, dt, steps, stride):
             state.tails[self.name] += steps
+
+        def set_schedule(self, occupancy_pct, chunks_per_warp=1, part=0):
+            state.schedules[self.name] = (occupancy_pct, chunks_per_warp, part)
 
         def observables(self):
             return np.array([[len(self.name)]])
@@ -137,6 +141,8 @@ def test_admission_budget_quanta_and_release(monkeypatch, workers):
     # whole quanta run as graph replays, the remainder as plain steps
     assert state.graph_launches == {"a": 200, "b": 100, "d": 300}
     assert state.tails == {"a": 50, "b": 0, "c": 40, "d": 20}
+    # larger requests run their stage kernels at half the CTA slots, leaving SMs to the batched ticks
+    assert set(state.schedules.values()) == {(50, 1, 0)}
     # each result carries its own run's observables
     assert all(res[i].observables[0, 0] == len(sizes_name) for i, sizes_name in ((0, "a"), (1, "b"), (4, "d")))
     s = stats.summary()
