@@ -93,16 +93,20 @@ __device__ __forceinline__ void cp_async8_hint(void *smem, const void *gmem, uin
   asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "l"(pol)
                : "memory");
 }
-// own tiles: streamed once
-__device__ __forceinline__ void warp_copy16_stream(void *dst, const void *src, int bytes, int lane) {
+// own tiles: streamed once (read_again: the same tiles are read a second time right after -- the first
+// stage of a step, where y is the input -- and keep the default priority)
+__device__ __forceinline__ void warp_copy16_stream(void *dst, const void *src, int bytes, int lane,
+                                                   bool read_again = false) {
 #if HEOM_L2_HINTS
-  const uint64_t pol = l2_evict_first();
-  char *d = reinterpret_cast<char *>(dst);
-  const char *s = reinterpret_cast<const char *>(src);
-  for (int o = lane * 16; o < bytes; o += 32 * 16) cp_async16_hint(d + o, s + o, pol);
-#else
-  warp_copy16(dst, src, bytes, lane);
+  if (!read_again) {
+    const uint64_t pol = l2_evict_first();
+    char *d = reinterpret_cast<char *>(dst);
+    const char *s = reinterpret_cast<const char *>(src);
+    for (int o = lane * 16; o < bytes; o += 32 * 16) cp_async16_hint(d + o, s + o, pol);
+    return;
+  }
 #endif
+  warp_copy16(dst, src, bytes, lane);
 }
 // gathered neighbour rows: kept for the neighbour's other links
 __device__ __forceinline__ void cp_async16_keep(void *smem, const void *gmem) {
@@ -200,10 +204,11 @@ struct WarpSmem {
 
 template <int N, typename CT, typename BT>
 __device__ __forceinline__ void issue_tiles(const typename Cplx<CT>::type *src_region, int own0, int u0, int cnt,
-                                            void *dst, int lane) {
+                                            void *dst, int lane, bool read_again = false) {
   using S = StageShape<N, CT, BT>;
   using C2 = typename Cplx<CT>::type;
-  warp_copy16_stream(dst, src_region + (int64_t)(u0 - own0) * S::EpOwn, cnt * S::EpOwn * (int)sizeof(C2), lane);
+  warp_copy16_stream(dst, src_region + (int64_t)(u0 - own0) * S::EpOwn, cnt * S::EpOwn * (int)sizeof(C2), lane,
+                     read_again);
 }
 
 // Copies W consecutive elements of neighbour v, from element e of its tile, to dst.  Elements of
@@ -517,6 +522,8 @@ __device__ __forceinline__ void stage_chunks(const Args &a, unsigned char *smem_
   const int li = lane - la * N;
   const bool lane_ok = la < A;
   const bool has_y = (c.y.head != nullptr) || (c.y.body != nullptr);
+  // y is the input (first stage of a step): the input tiles are read again as y right after
+  const bool same_y = c.y.head == c.zin.head && c.y.body == c.zin.body;
   const CT term_i = lane_ok ? a.term[li] : (CT)0;
   // terminator Delta_i + Delta_j of row li (0 on the diagonal), precomputed in FP64 where every FP64
   // add costs pipe time; FP32 recomputes it (the registers are worth more there)
@@ -552,7 +559,7 @@ __device__ __forceinline__ void stage_chunks(const Args &a, unsigned char *smem_
   if (first < n_chunks) {
     const int u0 = c.u_begin + first * A;
     const int cnt = min(A, c.u_end - u0);
-    issue_tiles<N, CT, BT>(zin_own, own0, u0, cnt, wb + W::tile0, lane);
+    issue_tiles<N, CT, BT>(zin_own, own0, u0, cnt, wb + W::tile0, lane, same_y);
     const int64_t lo = __shfl_sync(0xffffffffu, off_cur, 0), hi = __shfl_sync(0xffffffffu, off_cur, cnt);
     const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)cap), rbase, rlim);
     warp_copy16(wb + W::rec0, recs + (lo - rbase), nr * (int)sizeof(R), lane);
@@ -570,7 +577,7 @@ __device__ __forceinline__ void stage_chunks(const Args &a, unsigned char *smem_
     if (nx < n_chunks) {
       const int v0 = c.u_begin + nx * A;
       const int vcnt = min(A, c.u_end - v0);
-      issue_tiles<N, CT, BT>(zin_own, own0, v0, vcnt, wb + (b ? W::tile0 : W::tile1), lane);
+      issue_tiles<N, CT, BT>(zin_own, own0, v0, vcnt, wb + (b ? W::tile0 : W::tile1), lane, same_y);
       const int64_t lo = __shfl_sync(0xffffffffu, off_nxt, 0), hi = __shfl_sync(0xffffffffu, off_nxt, vcnt);
       const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)cap), rbase, rlim);
       warp_copy16(wb + (b ? W::rec0 : W::rec1), recs + (lo - rbase), nr * (int)sizeof(R), lane);

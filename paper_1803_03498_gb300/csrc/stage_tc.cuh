@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
   const int li = lane - la * N;
   const bool lane_ok = la < A;
   const bool has_y = c.y.body != nullptr;
+  const bool same_y = c.y.body == c.zin.body;  // first stage of a step: the input is read again as y
   const float term_i = lane_ok ? a.term[li] : 0.f;
   const C2 *zin_own = reinterpret_cast<const C2 *>(c.zin.body);
   C2 *out_own = reinterpret_cast<C2 *>(c.out.body);
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
   if (first < n_chunks) {
     const int u0 = c.u_begin + first * A;
     const int cnt = min(A, c.u_end - u0);
-    issue_tiles<N, float, float>(zin_own, own0, u0, cnt, wb + W::tile0, lane);
+    issue_tiles<N, float, float>(zin_own, own0, u0, cnt, wb + W::tile0, lane, same_y);
     const int64_t lo = __shfl_sync(0xffffffffu, off_cur, 0), hi = __shfl_sync(0xffffffffu, off_cur, cnt);
     const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)cap), rbase, c.n_recs);
     warp_copy16(wb + W::rec0, recs + (lo - rbase), nr * (int)sizeof(R), lane);
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, HEOM_TC_MIN_BLOCKS) stage_tc_ke
     if (nx < n_chunks) {
       const int v0 = c.u_begin + nx * A;
       const int vcnt = min(A, c.u_end - v0);
-      issue_tiles<N, float, float>(zin_own, own0, v0, vcnt, wb + (b ? W::tile0 : W::tile1), lane);
+      issue_tiles<N, float, float>(zin_own, own0, v0, vcnt, wb + (b ? W::tile0 : W::tile1), lane, same_y);
       const int64_t lo = __shfl_sync(0xffffffffu, off_nxt, 0), hi = __shfl_sync(0xffffffffu, off_nxt, vcnt);
       const int nr = heom_rec_batch(c.err, lo, (int)min(hi - lo, (int64_t)cap), rbase, c.n_recs);
       warp_copy16(wb + (b ? W::rec0 : W::rec1), recs + (lo - rbase), nr * (int)sizeof(R), lane);
