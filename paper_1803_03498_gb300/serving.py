@@ -7,7 +7,8 @@ A request is one propagation (system, rho(0), dt, steps).  The server
   * builds each admitted request's run (link records on the host, uploads, the CUDA graph) on a pool
     of `workers` host threads -- the library releases the interpreter lock, so several runs are set
     up at once while the main loop keeps launching;
-  * batches the RK4 steps of the small requests (mixed precision, at most `group_max_ados` ADOs): in
+  * batches the RK4 steps of the small requests (mixed precision, at most `group_max_ados` ADOs and
+    at most `group_max_cost` ADOs x n_states^2, so that no costly member stretches every tick): in
     each tick every admitted small request advances by up to `quantum` steps in one
     heom_group_propagate call, where the runs of equal n_states share one work-list launch per stage
     and part -- a few launches per step for all of them instead of eight per request; requests
@@ -93,7 +94,8 @@ class ServeStats:
 class Server:
     def __init__(self, budget_bytes: float = 120e9, precision: str = "fp32_mixed", quantum: int = 100,
                  max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False, graph_steps: int | None = None,
-                 workers: int = 4, group_max_ados: int = 200000, large_occupancy_pct: int = 50):
+                 workers: int = 4, group_max_ados: int = 200000, group_max_cost: float = 4e6,
+                 large_occupancy_pct: int = 100):
         if obs_stride > 0 and quantum % obs_stride:
             raise ValueError("obs_stride must divide quantum")
         if graph_steps is None:  # one graph per quantum (measured: fewer, longer graphs serve more)
@@ -110,8 +112,11 @@ class Server:
         self.workers = max(0, int(workers))
         # requests up to this many ADOs (mixed precision) advance in the batched ticks; 0: none
         self.group_max_ados = int(group_max_ados) if precision == "fp32_mixed" else 0
-        # a larger request's persistent stage kernels fill only this share of each SM's CTA slots, so
-        # that the small requests' launches find free SMs instead of waiting for whole launches of it
+        # and whose ADOs x n_states^2 (the work of one stage) is at most this: a tick lasts as long as its
+        # slowest member's steps, so one costly member would hold up every small request of the tick
+        self.group_max_cost = float(group_max_cost)
+        # below 100: a larger request's persistent stage kernels fill only this share of each SM's CTA
+        # slots (measured on the full mix: 50 % slowed the largest request more than it helped the rest)
         self.large_occupancy_pct = int(large_occupancy_pct)
         self._hier_cache = {}
 
@@ -122,7 +127,8 @@ class Server:
         return self._hier_cache[key]
 
     def _small(self, r) -> bool:
-        return r.prop.system.n_ado <= self.group_max_ados
+        s = r.prop.system
+        return s.n_ado <= self.group_max_ados and s.n_ado * s.N * s.N <= self.group_max_cost
 
     def _build(self, heom, r, hier, mr, st, dev):
         """Set up one admitted request on its stream: the run (host link records, uploads) and, for a
@@ -307,16 +313,25 @@ def main(argv=None):
     ap.add_argument("--workers", type=int, default=4, help="host threads that set up admitted requests")
     ap.add_argument("--quantum", type=int, default=100)
     ap.add_argument("--max-active", type=int, default=256, help="requests admitted at once (streams)")
+    ap.add_argument("--group-max-ados", type=int, default=200000, help="largest request batched in ticks")
+    ap.add_argument("--group-max-cost", type=float, default=4e6,
+                    help="largest ADOs x n_states^2 of a request batched in ticks")
+    ap.add_argument("--large-occupancy", type=int, default=100,
+                    help="share (%%) of each SM's CTA slots the stage kernels of a larger request fill")
     args = ap.parse_args(argv)
     heom.load()
     cap = args.max_ado_steps if args.max_ado_steps > 0 else None
     for rate in args.rates:
         reqs = wl.serving_stream(rate, args.requests, max_ado_steps=cap)
         st = Server(budget_bytes=args.budget, precision=args.precision, quantum=args.quantum,
-                    workers=args.workers, max_active=args.max_active).serve(reqs, real_time=True)
+                    workers=args.workers, max_active=args.max_active, group_max_ados=args.group_max_ados,
+                    group_max_cost=args.group_max_cost,
+                    large_occupancy_pct=args.large_occupancy).serve(reqs, real_time=True)
         s = st.summary()
         s.update({"offered_rate_req_per_s": rate, "max_ado_steps": cap, "precision": args.precision,
                   "workers": args.workers, "max_active": args.max_active, "quantum": args.quantum,
+                  "group_max_ados": args.group_max_ados, "group_max_cost": args.group_max_cost,
+                  "large_occupancy_pct": args.large_occupancy,
                   "rejected_fraction": s["rejected"] / max(s["requests"], 1)})
         print(json.dumps(s), flush=True)
     return 0

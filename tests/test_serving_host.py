@@ -127,8 +127,8 @@ def test_admission_budget_quanta_and_release(monkeypatch, workers):
     monkeypatch.setitem(__import__("sys").modules, "paper_1803_03498_gb300.heom", heom)
     monkeypatch.setattr(torch, "cuda", cuda)
     reqs = make_requests([("a", 250), ("b", 100), ("huge", 100), ("c", 40), ("d", 320)])
-    stats = serving.Server(budget_bytes=100, quantum=100, max_active=3, workers=workers,
-                           group_max_ados=0).serve(reqs, real_time=False)
+    stats = serving.Server(budget_bytes=100, quantum=100, max_active=3, workers=workers, group_max_ados=0,
+                           large_occupancy_pct=50).serve(reqs, real_time=False)
     res = {r.rid: r for r in stats.results}
     # the request larger than the whole budget is rejected at arrival, the rest complete
     assert res[2].rejected and "budget" in res[2].reason
