@@ -312,7 +312,8 @@ int heom_batch_destroy(heom_batch *b);
  * one launch per RK4 stage and part (FP64 head, FP32 body) covers every such run of that size, each
  * run's stage arguments staged from its own workspace, so many small requests cost a few launches
  * per step instead of eight each.  Other runs launch on their own, on the same stream.  Everything is
- * enqueued on cuda_stream, ordered after work already enqueued on each run's stream, and later work
+ * enqueued on cuda_stream (the launches of different sizes on library-created streams forked from and
+ * joined back into it, with its priority), ordered after work already enqueued on each run's stream, and later work
  * on each run's stream is ordered after it; the call does not block, except that writing a run's
  * work-list stage arguments (its first grouped call, or a new dt_fs) waits for cuda_stream.
  * Results equal heom_propagate's bit for bit: every ADO gets the same arithmetic in the same order.

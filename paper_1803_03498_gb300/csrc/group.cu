@@ -178,8 +178,12 @@ extern "C" int heom_group_propagate(heom_run *const *runs, int n_runs, double dt
     *out = gs;
     if (single) return HEOM_OK;
     if (!cls[n]) {
+      // the class streams take the caller's priority, so that a high-priority caller's ticks stay ahead
+      // of other streams' launches when SM slots free up
       cudaEvent_t fe = nullptr;
-      cudaError_t ce = cudaStreamCreateWithFlags(&cls[n], cudaStreamNonBlocking);
+      int prio = 0;
+      cudaError_t ce = cudaStreamGetPriority(gs, &prio);
+      if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&cls[n], cudaStreamNonBlocking, prio);
       if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&fe, cudaEventDisableTiming);
       if (ce == cudaSuccess) cls_ev.push_back(fe);
       if (ce == cudaSuccess) ce = cudaEventRecord(fe, gs);

@@ -191,7 +191,9 @@ class Server:
             free_streams.append(a.stream)
             active.remove(a)
 
-        group_stream = torch.cuda.Stream() if self.group_max_ados > 0 else None
+        # the ticks' stream has the higher priority: when SM slots free up, the block scheduler dispatches
+        # the small requests' launches before those of larger requests queued on the other streams
+        group_stream = torch.cuda.Stream(priority=-1) if self.group_max_ados > 0 else None
         tick = None  # event of the batched tick in flight
 
         while arrivals or pending or active or building or tick is not None:

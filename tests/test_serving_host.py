@@ -82,7 +82,8 @@ def fake_modules(state, sizes):
     heom.group_propagate = group_propagate
 
     class Stream:
-        pass
+        def __init__(self, priority=0):
+            self.priority = priority
 
     class Event:
         def record(self, st):
