@@ -417,9 +417,10 @@ def time_serving(rates=(5.0, 20.0, 50.0), n_requests=100, max_ado_steps=2e7, bud
     return {"workload": f"Poisson arrivals, N 2..24, D 2..6, K 0..1, 200..5000 steps, fp32_mixed; timed legs: "
                         f"{n_requests} requests redrawn to <= {max_ado_steps:.0e} ADOs x steps (the narrowed mix; "
                         f"the full mix is measured by the serving module's rate sweep with --max-ado-steps 0)",
-            "server": f"up to {max_active} requests admitted; small requests (<= 200,000 ADOs) advance in batched "
-                      f"ticks of one heom_group_propagate call (work-list launches per size class), larger ones "
-                      f"on their own streams with CUDA graphs; quantum 100 steps",
+            "server": f"up to {max_active} requests admitted; small requests (<= 200,000 ADOs and <= 4e6 ADOs x "
+                      f"n_states^2) advance in batched ticks of one heom_group_propagate call (work-list launches "
+                      f"per size class) on a high-priority stream, larger ones on their own streams with CUDA "
+                      f"graphs; quantum 100 steps",
             "budget_bytes": budget, "full_mix_rejected_fraction": rej / len(full), "legs": legs}
 
 

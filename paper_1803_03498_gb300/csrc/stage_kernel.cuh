@@ -181,8 +181,10 @@ struct StageShape {
   static constexpr int EpOwn = kOwnHead ? E : EpBody;
   static constexpr bool kRowRegs = N <= 16;                                // H row in registers
   static constexpr bool kPairs = sizeof(CT) == 4 && (N % 2) == 0;          // 16-byte tile row loads
-  // FP32 kernels with the row in registers add the links there, one lane per (ADO, state)
-  static constexpr bool kOwnerLinks = sizeof(CT) == 4 && kRowRegs;
+  // FP32 kernels add the links to the row in registers, one lane per (ADO, state); for N > 16 (one ADO
+  // per warp) this path also keeps H out of lane-dependent loads: S = s H reads H uniformly
+  static constexpr bool kOwnerLinks = sizeof(CT) == 4;
+  static_assert(!kOwnerLinks || A * N <= 32, "owner lanes index the 32-entry owner table");
 };
 
 // Per-warp shared-memory layout (byte offsets).

@@ -274,3 +274,34 @@ def test_column_kernel_sizes_fp64(N, K, D):
 def _sym(rng, N):
     H = np.diag(rng.uniform(0.0, 400.0, N)) + np.triu(rng.normal(0.0, 40.0, (N, N)), 1)
     return H + np.triu(H, 1).T
+
+
+@pytest.mark.parametrize("N", [17, 19, 20, 24])
+def test_fp32_owner_path_large_n(N):
+    """FP32 body kernels for 17 <= N <= 24 (one ADO per warp, N of 32 lanes) on Hermitian runs take the
+    owner-lane form: S = s H from each lane's own row, the links added in registers, Q + Q^dagger at
+    the end.  K = 0, D = 3 (levels 2 and 3 in the FP32 body, ragged last chunks).  (1) One right-hand
+    side of a dense Hermitian random state, every ADO, against the oracle (2e-5 of the largest
+    element: FP32 rounding of an N-term sum per element); (2) 30 RK4 steps from the first site on
+    populations (1e-6)."""
+    from paper_1803_03498_gb300 import heom
+    rng = np.random.default_rng(1803200 + N)
+    H = _sym(rng, N)
+    s = wl.System(f"owner N={N}", H, list(range(N)), [35.0] * N, [60.0] * N, [300.0] * N, K=0, D=3)
+    rho = np.zeros((N, N))
+    rho[0, 0] = 1.0
+    p = wl.Propagation(s, rho, np.zeros((N, N)), 1.0, 30)
+    m = oracle_for(s)
+    re, im = hermitian(*wl.random_state(m.n_ado, N, seed=N, scale=0.1))
+    r = heom.Run(s, p.rho0_re, p.rho0_im, precision="fp32_mixed", max_records=2)
+    r.set_ados(0, re, im)
+    gre0, gim0 = r.get_ados(0, m.n_ado)  # the state as the GPU holds it (body rounded to FP32)
+    ore, oim = m.rhs(gre0, gim0)
+    gre, gim = r.rhs_eval(0, m.n_ado)
+    ref = ore + 1j * oim
+    assert np.max(np.abs(gre + 1j * gim - ref)) <= 2e-5 * np.max(np.abs(ref))
+    r.close()
+    m2, ore2, oim2, oobs = oracle_propagate(p, p.n_steps, stride=3)
+    r2, gobs = gpu_run(p, "fp32_mixed", stride=3)
+    assert np.max(np.abs(gobs[:, :N] - oobs[:, :N])) <= POP_TOL
+    assert np.max(np.abs(ore2[-1] + 1j * oim2[-1])) > 0  # the deepest ADOs were reached
