@@ -331,8 +331,11 @@ int heom_group_propagate(heom_run *const *runs, int n_runs, double dt_fs, const 
  * map the same arithmetic onto the GPU differently).  A stage launch covers its ADOs in chunks of
  * floor(32 / n_states) consecutive ADOs over a persistent grid of CTAs.  A schedule fixes what the
  * arithmetic leaves open:
- *   occupancy_pct     1..100: the grid is sized for this percentage of the kernel's CTAs that fit
- *                     on one SM (rounded down, at least 1) times the SM count;
+ *   occupancy_pct     1..1600: the grid is sized for this percentage of the kernel's CTAs that fit
+ *                     on one SM (rounded down, at least 1) times the SM count.  Above 100 the grid
+ *                     is several waves of CTAs that retire while the launch runs, so that launches
+ *                     on other (higher-priority) streams get SM slots before it ends, at the cost
+ *                     of more CTA starts;
  *   chunks_per_warp   1, 2 or 4: column-0 kernels (heom_run_layout 1) let each warp hold this many
  *                     consecutive chunks at once (capped at 32 ADOs per warp: 2 for n_states 2, 3
  *                     for 3), one element of each per lane, and load the link records and

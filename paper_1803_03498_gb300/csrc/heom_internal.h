@@ -108,9 +108,11 @@ extern thread_local int g_tune_suppress;
 // g, capped so that a step holds at most 32 ADOs (a link record names its ADO by u mod 32).
 __host__ __device__ constexpr int vec_group(int n, int g) { return g < 32 / (32 / n) ? g : 32 / (32 / n); }
 
-// CTAs per SM of a persistent grid for a schedule's occupancy percentage (at least 1).
+// CTAs per SM of the grid for a schedule's occupancy percentage (at least 1): up to 100 a persistent
+// grid filling that share of each SM's CTA slots; above 100 that many percent of one resident wave,
+// so that CTAs retire while the launch runs.
 inline int sched_ctas(int per_sm, int occ_pct) {
-  const int b = (occ_pct <= 0 || occ_pct >= 100) ? per_sm : per_sm * occ_pct / 100;
+  const int b = occ_pct <= 0 ? per_sm : per_sm * occ_pct / 100;
   return b < 1 ? 1 : b;
 }
 

@@ -51,7 +51,7 @@ std::vector<heom_schedule> candidates(int layout) {
 }
 
 static bool valid_schedule(const heom_schedule &s) {
-  return s.occupancy_pct >= 1 && s.occupancy_pct <= 100 &&
+  return s.occupancy_pct >= 1 && s.occupancy_pct <= 1600 &&
          (s.chunks_per_warp == 1 || s.chunks_per_warp == 2 || s.chunks_per_warp == 4);
 }
 
@@ -177,7 +177,7 @@ extern "C" int heom_get_schedule(const heom_run *r, int part, heom_schedule *out
 
 extern "C" int heom_set_schedule(heom_run *r, int part, const heom_schedule *s) {
   if (!r || !s || part < 0 || part > 1 || (part == 1 && r->precision == HEOM_FP64) || !valid_schedule(*s)) {
-    set_error("heom_set_schedule: need a run, part 0 or 1 (1 only with an FP64 head), occupancy_pct 1..100, "
+    set_error("heom_set_schedule: need a run, part 0 or 1 (1 only with an FP64 head), occupancy_pct 1..1600, "
               "chunks_per_warp 1, 2 or 4");
     return HEOM_E_ARG;
   }

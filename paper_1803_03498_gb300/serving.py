@@ -95,7 +95,7 @@ class Server:
     def __init__(self, budget_bytes: float = 120e9, precision: str = "fp32_mixed", quantum: int = 100,
                  max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False, graph_steps: int | None = None,
                  workers: int = 4, group_max_ados: int = 200000, group_max_cost: float = 4e6,
-                 large_occupancy_pct: int = 100):
+                 large_occupancy_pct: int = 800):
         if obs_stride > 0 and quantum % obs_stride:
             raise ValueError("obs_stride must divide quantum")
         if graph_steps is None:  # one graph per quantum (measured: fewer, longer graphs serve more)
@@ -115,8 +115,11 @@ class Server:
         # and whose ADOs x n_states^2 (the work of one stage) is at most this: a tick lasts as long as its
         # slowest member's steps, so one costly member would hold up every small request of the tick
         self.group_max_cost = float(group_max_cost)
-        # below 100: a larger request's persistent stage kernels fill only this share of each SM's CTA
-        # slots (measured on the full mix: 50 % slowed the largest request more than it helped the rest)
+        # the schedule of a larger request's stage launches (heom_set_schedule's occupancy_pct): above 100
+        # its grid is several waves of CTAs that retire while the launch runs, so the ticks' launches on
+        # the high-priority stream take SM slots within microseconds instead of waiting for the whole
+        # launch; below 100 a persistent grid on that share of each SM's CTA slots (measured on the full
+        # mix: 50 % slowed the largest request more than it helped the rest)
         self.large_occupancy_pct = int(large_occupancy_pct)
         self._hier_cache = {}
 
@@ -140,7 +143,7 @@ class Server:
         with torch.cuda.stream(st):
             run = heom.Run(r.prop.system, r.prop.rho0_re, r.prop.rho0_im, precision=self.precision,
                            w=r.prop.w, max_records=mr, hier=hier, stream=st)
-            if not self._small(r) and 0 < self.large_occupancy_pct < 100:
+            if not self._small(r) and self.large_occupancy_pct != 100:
                 run.set_schedule(self.large_occupancy_pct, 1, part=0)
             graph = None
             if r.prop.n_steps >= self.quantum and not self._small(r):
@@ -318,8 +321,8 @@ def main(argv=None):
     ap.add_argument("--group-max-ados", type=int, default=200000, help="largest request batched in ticks")
     ap.add_argument("--group-max-cost", type=float, default=4e6,
                     help="largest ADOs x n_states^2 of a request batched in ticks")
-    ap.add_argument("--large-occupancy", type=int, default=100,
-                    help="share (%%) of each SM's CTA slots the stage kernels of a larger request fill")
+    ap.add_argument("--large-occupancy", type=int, default=800,
+                    help="occupancy_pct of a larger request's stage launches (above 100: waves of CTAs)")
     args = ap.parse_args(argv)
     heom.load()
     cap = args.max_ado_steps if args.max_ado_steps > 0 else None

@@ -66,7 +66,7 @@ def test_every_schedule_gives_identical_results(heom, case):
     ref = run_with(heom, prop, precision, cands[0])
     assert ref[3] == layout
     assert np.all(np.isfinite(ref[1])) and np.max(np.abs(ref[1][1:])) > 0  # the hierarchy is populated
-    for c in cands[1:]:
+    for c in cands[1:] + [(400, 1)]:  # the tuner's candidates and an oversubscribed grid
         out = run_with(heom, prop, precision, c)
         for a, b in zip(ref[:3], out[:3]):
             assert np.array_equal(a, b), (case, c)
@@ -105,7 +105,7 @@ def test_tune_keeps_state_and_picks_fastest(heom, kind):
 def test_schedule_argument_errors(heom):
     p, _ = wl.fmo_like()
     r = heom.Run(p.system, p.rho0_re, p.rho0_im, precision="fp64", max_records=4)
-    for bad in [(0, 1), (101, 1), (100, 3), (100, 0)]:
+    for bad in [(0, 1), (1601, 1), (100, 3), (100, 0)]:
         with pytest.raises(heom.HeomError) as ei:
             r.set_schedule(*bad)
         assert ei.value.code == heom.HEOM_E_ARG

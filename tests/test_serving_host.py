@@ -115,8 +115,8 @@ def make_requests(spec):
     return reqs
 
 
-@pytest.mark.parametrize("workers", [0, 2])
-def test_admission_budget_quanta_and_release(monkeypatch, workers):
+@pytest.mark.parametrize("workers,pct", [(0, 50), (2, 50), (2, 800)])
+def test_admission_budget_quanta_and_release(monkeypatch, workers, pct):
     import torch
 
     import paper_1803_03498_gb300 as pkg
@@ -129,7 +129,7 @@ def test_admission_budget_quanta_and_release(monkeypatch, workers):
     monkeypatch.setattr(torch, "cuda", cuda)
     reqs = make_requests([("a", 250), ("b", 100), ("huge", 100), ("c", 40), ("d", 320)])
     stats = serving.Server(budget_bytes=100, quantum=100, max_active=3, workers=workers, group_max_ados=0,
-                           large_occupancy_pct=50).serve(reqs, real_time=False)
+                           large_occupancy_pct=pct).serve(reqs, real_time=False)
     res = {r.rid: r for r in stats.results}
     # the request larger than the whole budget is rejected at arrival, the rest complete
     assert res[2].rejected and "budget" in res[2].reason
@@ -142,8 +142,9 @@ def test_admission_budget_quanta_and_release(monkeypatch, workers):
     # whole quanta run as graph replays, the remainder as plain steps
     assert state.graph_launches == {"a": 200, "b": 100, "d": 300}
     assert state.tails == {"a": 50, "b": 0, "c": 40, "d": 20}
-    # larger requests run their stage kernels at half the CTA slots, leaving SMs to the batched ticks
-    assert set(state.schedules.values()) == {(50, 1, 0)}
+    # every larger request's body launches take the given schedule (50: half the CTA slots of each SM;
+    # 800: eight waves of CTAs that retire while the launch runs)
+    assert set(state.schedules.values()) == {(pct, 1, 0)} and len(state.schedules) == 4
     # each result carries its own run's observables
     assert all(res[i].observables[0, 0] == len(sizes_name) for i, sizes_name in ((0, "a"), (1, "b"), (4, "d")))
     s = stats.summary()
@@ -175,6 +176,7 @@ def test_small_requests_advance_in_batched_ticks(monkeypatch, workers):
     stats = serving.Server(budget_bytes=100, quantum=100, max_active=4, workers=workers).serve(reqs, real_time=False)
     assert all(not r.rejected and np.isfinite(r.done_s) for r in stats.results)
     assert state.grouped == {"a": 250, "b": 100, "c": 40}
+    assert state.schedules == {}  # batched requests keep their own schedules
     assert state.graph_launches == {} and all(v == 0 for v in state.tails.values())
     # no tick advances a request by more than a quantum, and the first tick covers everything admitted
     assert all(q <= 100 for t in state.ticks for q in t.values())
