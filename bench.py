@@ -197,6 +197,34 @@ def time_gpu(prop, precision, steps, warmup, ws, clocks=None, schedule=None):
     return ms, launches, kt, obs, clk
 
 
+def time_states(steps, warmup, ws, states=(14, 17, 19, 20, 22, 24), max_ados=2.5e6):
+    """Mixed-precision rate across n_states: population runs from the first site of seeded random
+    systems (one bath per site, K = 0, the deepest hierarchy with at most max_ados ADOs: every state
+    copy larger than L2).  Per size: ADO-RHS evals/s, the body launch time and its bandwidth on the
+    per-unit count (4 tile transfers of N^2 FP32 complex elements + 2 M link-table entries per
+    evaluation)."""
+    from math import comb
+
+    from paper_1803_03498_gb300 import workloads as wl
+
+    rows = []
+    for N in states:
+        D = 1
+        while comb(N + D + 1, D + 1) <= max_ados:
+            D += 1
+        sysm = wl._random_system(np.random.default_rng(1000 + N), N, D, 0, f"random N={N} K=0 D={D}")
+        re, im = wl._pure(N, 0)
+        prop = wl.Propagation(sysm, re, im, 0.5, steps, tag="states")
+        ms, _, kt, _, _ = time_gpu(prop, "fp32_mixed", steps, warmup, ws)
+        body_ms = kt["ms"] / max(kt["launches"], 1)
+        nb = sysm.n_ado - (1 + sysm.n_modes)
+        unit = nb * (4.0 * N * N * 8 + 2 * sysm.n_modes * 4)
+        rows.append({"n_states": N, "depth": D, "n_ado": sysm.n_ado, "ms_per_step": ms / steps,
+                     "evals_per_s": sysm.n_ado * 4 * steps / (ms / 1000.0), "body_launch_ms": body_ms,
+                     "per_unit_GBs": unit / (body_ms / 1000.0) / 1e9})
+    return rows
+
+
 def fp64_and_gate(prop, gate_steps, warmup, ws, clocks):
     """The FP64 path over the configuration's full length, and the mixed-precision error gate.
 
@@ -502,10 +530,11 @@ def main():
                          "1000 steps of 1 fs); its steps after the warm-up time the FP64 path (0: skip both)")
     ap.add_argument("--depth", type=int, default=0, help="override the hierarchy depth (profiling cases)")
     ap.add_argument("--tc-steps", type=int, default=0, help="timed steps of the split-TF32 variant (0: steps/10)")
-    ap.add_argument("--only", default="", choices=["", "mixed", "fp64", "split_tf32", "dipole", "field"],
+    ap.add_argument("--only", default="", choices=["", "mixed", "fp64", "split_tf32", "dipole", "field", "states"],
                     help="one case only, no end-to-end or CPU legs, no autotuning (profiling cases): a precision "
                          "of the LHCII-like population run, its linear-absorption run (dipole: 15 states, column-0 "
-                         "layout, mixed), or the pumped two-exciton leg (field)")
+                         "layout, mixed), the pumped two-exciton leg (field), or the mixed-precision rate across "
+                         "n_states (states)")
     ap.add_argument("--schedule", default="", help="profiling cases: occupancy%%,chunks_per_warp of the body launches")
     args = ap.parse_args()
     ws, rank, local = _dist()
@@ -540,6 +569,11 @@ def main():
             if rank == 0:
                 print(json.dumps({"profile_case": "two_exciton_field", **time_field(steps=args.steps,
                                                                                    warmup=args.warmup)}), flush=True)
+            return 0
+        if args.only == "states":
+            rows = time_states(args.steps, args.warmup, ws)
+            if rank == 0:
+                print(json.dumps({"profile_case": "n_states sweep", "rows": rows}), flush=True)
             return 0
         sched = tuple(int(x) for x in args.schedule.split(",")) if args.schedule else None
         prec = {"mixed": "fp32_mixed", "fp64": "fp64", "split_tf32": "split_tf32", "dipole": "fp32_mixed"}[args.only]
