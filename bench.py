@@ -331,9 +331,11 @@ def time_batch(steps=20, per_launch=10):
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("batch_timed")  # lets a profiler select the timed replays
     e0.record(st)
     b.launch(steps // per_launch)
     e1.record(st)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms_batch = e0.elapsed_time(e1)
     layout = ("every run in the column-0 (coherence-block) layout" if all(r.layout() == 1 for r in runs)
@@ -530,11 +532,12 @@ def main():
                          "1000 steps of 1 fs); its steps after the warm-up time the FP64 path (0: skip both)")
     ap.add_argument("--depth", type=int, default=0, help="override the hierarchy depth (profiling cases)")
     ap.add_argument("--tc-steps", type=int, default=0, help="timed steps of the split-TF32 variant (0: steps/10)")
-    ap.add_argument("--only", default="", choices=["", "mixed", "fp64", "split_tf32", "dipole", "field", "states"],
+    ap.add_argument("--only", default="", choices=["", "mixed", "fp64", "split_tf32", "dipole", "field", "states",
+                                                   "batch"],
                     help="one case only, no end-to-end or CPU legs, no autotuning (profiling cases): a precision "
                          "of the LHCII-like population run, its linear-absorption run (dipole: 15 states, column-0 "
                          "layout, mixed), the pumped two-exciton leg (field), or the mixed-precision rate across "
-                         "n_states (states)")
+                         "n_states (states), or the ragged batch (batch: autotuned as in the full run)")
     ap.add_argument("--schedule", default="", help="profiling cases: occupancy%%,chunks_per_warp of the body launches")
     args = ap.parse_args()
     ws, rank, local = _dist()
@@ -563,6 +566,10 @@ def main():
         prop.system.D = args.depth
         prop.system.name = prop.system.name.replace("D=6", f"D={args.depth}")
     n_ado = prop.system.n_ado
+    if args.only == "batch":
+        if rank == 0:
+            print(json.dumps({"profile_case": "ragged_batch", **time_batch(steps=args.steps)}), flush=True)
+        return 0
     if args.only:
         heom.set_autotune(0)  # the same launches every time: no tuning probes before the captured ones
         if args.only == "field":
