@@ -39,11 +39,14 @@ class Result:
     rid: int
     arrival_s: float
     admitted_s: float = float("nan")
+    active_s: float = float("nan")  # set-up done: the request's steps start to be enqueued
     done_s: float = float("nan")
     rejected: bool = False
     reason: str = ""
     n_ado: int = 0
+    n_states: int = 0
     n_steps: int = 0
+    batched: bool = False  # advanced in the batched ticks
     workspace_bytes: int = 0
     observables: np.ndarray | None = None
     sigma0: np.ndarray | None = None
@@ -51,6 +54,13 @@ class Result:
     @property
     def latency_s(self) -> float:
         return self.done_s - self.arrival_s
+
+    def record(self) -> dict:
+        """The scalar fields (one line of a per-request log)."""
+        return {"rid": self.rid, "arrival_s": self.arrival_s, "admitted_s": self.admitted_s,
+                "active_s": self.active_s, "done_s": self.done_s, "latency_s": self.latency_s,
+                "rejected": self.rejected, "n_ado": self.n_ado, "n_states": self.n_states,
+                "n_steps": self.n_steps, "batched": self.batched, "workspace_bytes": self.workspace_bytes}
 
 
 @dataclass
@@ -175,6 +185,8 @@ class Server:
             return time.perf_counter() - t0
 
         def activate(r, si, res, run, graph):
+            res.active_s = now()
+            res.batched = self._small(r)
             ev = torch.cuda.Event()
             ev.record(streams[si])
             active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph, self._small(r)))
@@ -204,7 +216,7 @@ class Server:
             while arrivals and (not real_time or arrivals[0].arrival_s <= t):
                 r = arrivals.popleft()
                 res = Result(r.rid, r.arrival_s if real_time else 0.0, n_ado=r.prop.system.n_ado,
-                             n_steps=r.prop.n_steps)
+                             n_states=r.prop.system.N, n_steps=r.prop.n_steps)
                 results[r.rid] = res
                 s = r.prop.system
                 # a large hierarchy whose three state copies alone exceed the budget is rejected
@@ -321,6 +333,7 @@ def main(argv=None):
     ap.add_argument("--group-max-ados", type=int, default=200000, help="largest request batched in ticks")
     ap.add_argument("--group-max-cost", type=float, default=4e6,
                     help="largest ADOs x n_states^2 of a request batched in ticks")
+    ap.add_argument("--dump", default="", help="write every request's timeline to <dump>_<rate>.jsonl")
     ap.add_argument("--large-occupancy", type=int, default=800,
                     help="occupancy_pct of a larger request's stage launches (above 100: waves of CTAs)")
     args = ap.parse_args(argv)
@@ -333,6 +346,10 @@ def main(argv=None):
                     group_max_cost=args.group_max_cost,
                     large_occupancy_pct=args.large_occupancy).serve(reqs, real_time=True)
         s = st.summary()
+        if args.dump:
+            with open(f"{args.dump}_{rate:g}.jsonl", "w") as fh:
+                for res in st.results:
+                    fh.write(json.dumps(res.record()) + "\n")
         s.update({"offered_rate_req_per_s": rate, "max_ado_steps": cap, "precision": args.precision,
                   "workers": args.workers, "max_active": args.max_active, "quantum": args.quantum,
                   "group_max_ados": args.group_max_ados, "group_max_cost": args.group_max_cost,

@@ -145,6 +145,7 @@ def test_admission_budget_quanta_and_release(monkeypatch, workers, pct):
     # every larger request's body launches take the given schedule (50: half the CTA slots of each SM;
     # 800: eight waves of CTAs that retire while the launch runs)
     assert set(state.schedules.values()) == {(pct, 1, 0)} and len(state.schedules) == 4
+    assert not any(r.batched for r in stats.results)
     # each result carries its own run's observables
     assert all(res[i].observables[0, 0] == len(sizes_name) for i, sizes_name in ((0, "a"), (1, "b"), (4, "d")))
     s = stats.summary()
@@ -177,6 +178,8 @@ def test_small_requests_advance_in_batched_ticks(monkeypatch, workers):
     assert all(not r.rejected and np.isfinite(r.done_s) for r in stats.results)
     assert state.grouped == {"a": 250, "b": 100, "c": 40}
     assert state.schedules == {}  # batched requests keep their own schedules
+    assert all(r.batched and r.arrival_s <= r.admitted_s <= r.active_s <= r.done_s for r in stats.results)
+    assert set(stats.results[0].record()) >= {"rid", "latency_s", "n_states", "batched", "active_s"}
     assert state.graph_launches == {} and all(v == 0 for v in state.tails.values())
     # no tick advances a request by more than a quantum, and the first tick covers everything admitted
     assert all(q <= 100 for t in state.ticks for q in t.values())
