@@ -89,10 +89,6 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
   const int64_t rlim = kOwnHead ? c.rec_split : c.n_recs;  // records [rbase, rlim) of this region
   const int u0 = c.u_begin + step * SA;
   const int cnt = min(SA, c.u_end - u0);
-  // The step's memory round trips, issued as early as their inputs allow: the columns and the link
-  // offsets together, then the first window's records, which are in flight during H x below (the
-  // warp barriers there would otherwise keep these loads behind it)
-  const int64_t lo = c.link_off[u0], hi = c.link_off[u0 + cnt];
   C2 x[GE], yv[GE];
   CT rr[GE], ri[GE];
 #pragma unroll
@@ -105,13 +101,6 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
       x[g] = vec_load<N, CT, BT>(c.zin, c.u_split, u0 + a, li);
       if (has_y) yv[g] = vec_load<N, CT, BT>(c.y, c.u_split, u0 + a, li);
     }
-  }
-  LinkRec<CT> rq[GE];  // the records of the current window of 32 GE
-#pragma unroll
-  for (int q = 0; q < GE; ++q) {
-    const int64_t t = lo + q * 32 + lane;
-    rq[q].v = -1;
-    if (t < hi && HEOM_IN_RANGE(c.err, t, rbase, rlim)) rq[q] = recs[t - rbase];
   }
   // -i (H x)_i + i H_00 x_i, then decay and terminator; the columns go through shared memory (every
   // lane of an ADO reads the same word: one broadcast load per term)
@@ -143,14 +132,14 @@ __device__ __forceinline__ void vec_step(const StageCommon &c, const CT (&hrow)[
   // window's list holds record base + k, the owner's entries are contiguous (records sorted by ADO
   // and state), and the owner adds its segment in order
   {
+    const int64_t lo = c.link_off[u0], hi = c.link_off[u0 + cnt];
     for (int64_t base = lo; base < hi; base += 32 * GE) {
-      if (base != lo) {  // later windows (the first one was loaded above)
+      LinkRec<CT> rq[GE];
 #pragma unroll
-        for (int q = 0; q < GE; ++q) {
-          const int64_t t = base + q * 32 + lane;
-          rq[q].v = -1;
-          if (t < hi && HEOM_IN_RANGE(c.err, t, rbase, rlim)) rq[q] = recs[t - rbase];
-        }
+      for (int q = 0; q < GE; ++q) {
+        const int64_t t = base + q * 32 + lane;
+        rq[q].v = -1;
+        if (t < hi && HEOM_IN_RANGE(c.err, t, rbase, rlim)) rq[q] = recs[t - rbase];
       }
       int owner[GE];
       CT cr[GE], ci[GE];
