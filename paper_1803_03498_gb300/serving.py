@@ -48,6 +48,8 @@ class Result:
     n_steps: int = 0
     batched: bool = False  # advanced in the batched ticks
     workspace_bytes: int = 0
+    setup_run_s: float = 0.0    # set-up thread: run creation (host tables, uploads, autotuning)
+    setup_graph_s: float = 0.0  # set-up thread: CUDA graph capture
     observables: np.ndarray | None = None
     sigma0: np.ndarray | None = None
 
@@ -60,7 +62,8 @@ class Result:
         return {"rid": self.rid, "arrival_s": self.arrival_s, "admitted_s": self.admitted_s,
                 "active_s": self.active_s, "done_s": self.done_s, "latency_s": self.latency_s,
                 "rejected": self.rejected, "n_ado": self.n_ado, "n_states": self.n_states,
-                "n_steps": self.n_steps, "batched": self.batched, "workspace_bytes": self.workspace_bytes}
+                "n_steps": self.n_steps, "batched": self.batched, "workspace_bytes": self.workspace_bytes,
+                "setup_run_s": self.setup_run_s, "setup_graph_s": self.setup_graph_s}
 
 
 @dataclass
@@ -80,6 +83,8 @@ class _Active:
 class ServeStats:
     results: list = field(default_factory=list)
     wall_s: float = 0.0
+    # host time of the serving loop's parts: name -> [total s, longest single s, count]
+    loop: dict = field(default_factory=dict)
 
     def completed(self):
         return [r for r in self.results if not r.rejected and not np.isnan(r.done_s)]
@@ -151,14 +156,16 @@ class Server:
         if dev is not None:
             torch.cuda.set_device(dev)
         with torch.cuda.stream(st):
+            t0 = time.perf_counter()
             run = heom.Run(r.prop.system, r.prop.rho0_re, r.prop.rho0_im, precision=self.precision,
                            w=r.prop.w, max_records=mr, hier=hier, stream=st)
             if not self._small(r) and self.large_occupancy_pct != 100:
                 run.set_schedule(self.large_occupancy_pct, 1, part=0)
+            t1 = time.perf_counter()
             graph = None
             if r.prop.n_steps >= self.quantum and not self._small(r):
                 graph = heom.Batch([run], r.prop.dt_fs, self.graph_steps, self.obs_stride)
-        return run, graph
+        return run, graph, t1 - t0, time.perf_counter() - t1
 
     def serve(self, requests, real_time: bool = True) -> ServeStats:
         """Serve `requests` (workloads.Request: arrival_s, prop, rid) and return per-request results.
@@ -184,7 +191,24 @@ class Server:
         def now():
             return time.perf_counter() - t0
 
-        def activate(r, si, res, run, graph):
+        loop = {}
+
+        class timed:  # host time of one part of the loop
+            def __init__(self, name):
+                self.name = name
+
+            def __enter__(self):
+                self.t = time.perf_counter()
+
+            def __exit__(self, *exc):
+                d = time.perf_counter() - self.t
+                e = loop.setdefault(self.name, [0.0, 0.0, 0])
+                e[0] += d
+                e[1] = max(e[1], d)
+                e[2] += 1
+
+        def activate(r, si, res, run, graph, t_run=0.0, t_graph=0.0):
+            res.setup_run_s, res.setup_graph_s = t_run, t_graph
             res.active_s = now()
             res.batched = self._small(r)
             ev = torch.cuda.Event()
@@ -225,10 +249,11 @@ class Server:
                 if s.n_ado > 2_000_000 and 3 * s.n_ado * s.N * s.N * elem > self.budget:
                     res.rejected, res.reason = True, "workspace above the device-memory budget"
                     continue
-                hier = self._hier(heom, s.n_modes, s.D)
                 mr = (r.prop.n_steps // self.obs_stride + 2) if self.obs_stride > 0 else 2
                 try:
-                    res.workspace_bytes = heom.run_bytes(s, hier, self.precision, mr)
+                    with timed("arrival: hierarchy and workspace size"):
+                        hier = self._hier(heom, s.n_modes, s.D)
+                        res.workspace_bytes = heom.run_bytes(s, hier, self.precision, mr)
                 except heom.HeomError as e:
                     res.rejected, res.reason = True, str(e)
                     continue
@@ -246,17 +271,20 @@ class Server:
                     si = free_streams.pop()
                     used += res.workspace_bytes
                     res.admitted_s = now()
-                    if pool is None:
-                        activate(r, si, res, *self._build(heom, r, hier, mr, streams[si], None))
-                    else:
-                        building.append((pool.submit(self._build, heom, r, hier, mr, streams[si], dev), r, si, res))
+                    with timed("admission: set-up (inline) or its submission"):
+                        if pool is None:
+                            activate(r, si, res, *self._build(heom, r, hier, mr, streams[si], None))
+                        else:
+                            building.append((pool.submit(self._build, heom, r, hier, mr, streams[si], dev), r, si,
+                                             res))
                 else:
                     i += 1
             # set-ups that finished become active
             for b in [b for b in building if b[0].done()]:
                 building.remove(b)
                 fut, r, si, res = b
-                activate(r, si, res, *fut.result())
+                with timed("activation"):
+                    activate(r, si, res, *fut.result())
             # batched tick of the small requests: when the previous one is done, finished requests
             # complete and every other small request advances by up to a quantum in one call
             progressed = False
@@ -264,7 +292,8 @@ class Server:
                 tick = None
                 small = [a for a in active if a.small]
                 for a in [a for a in small if a.remaining == 0]:
-                    complete(a)
+                    with timed("completion (batched)"):
+                        complete(a)
                     progressed = True
                 by_dt = {}
                 for a in small:
@@ -272,7 +301,9 @@ class Server:
                         by_dt.setdefault(a.req.prop.dt_fs, []).append(a)
                 for dt, members in by_dt.items():
                     steps = [min(self.quantum, a.remaining) for a in members]
-                    heom.group_propagate([a.run for a in members], dt, steps, self.obs_stride, stream=group_stream)
+                    with timed("tick: heom_group_propagate"):
+                        heom.group_propagate([a.run for a in members], dt, steps, self.obs_stride,
+                                             stream=group_stream)
                     for a, q in zip(members, steps):
                         a.remaining -= q
                 if by_dt:
@@ -286,23 +317,25 @@ class Server:
                 progressed = True
                 if a.remaining > 0:
                     st = streams[a.stream]
-                    if a.graph is not None and a.remaining >= self.quantum:
-                        a.graph.launch(self.quantum // self.graph_steps)
-                        q = self.quantum
-                    else:
-                        q = a.remaining
-                        a.run.propagate(a.req.prop.dt_fs, q, self.obs_stride)
-                    a.remaining -= q
-                    a.event = torch.cuda.Event()
-                    a.event.record(st)
+                    with timed("quantum launch (larger requests)"):
+                        if a.graph is not None and a.remaining >= self.quantum:
+                            a.graph.launch(self.quantum // self.graph_steps)
+                            q = self.quantum
+                        else:
+                            q = a.remaining
+                            a.run.propagate(a.req.prop.dt_fs, q, self.obs_stride)
+                        a.remaining -= q
+                        a.event = torch.cuda.Event()
+                        a.event.record(st)
                 else:
-                    complete(a)
+                    with timed("completion (larger requests)"):
+                        complete(a)
             if not progressed:
                 if arrivals and real_time and not active and not pending and not building:
                     time.sleep(max(0.0, min(arrivals[0].arrival_s - now(), 0.01)))
                 else:
                     time.sleep(0.0002)
-        stats = ServeStats(results=[results[k] for k in sorted(results)], wall_s=now())
+        stats = ServeStats(results=[results[k] for k in sorted(results)], wall_s=now(), loop=loop)
         if pool is not None:
             pool.shutdown(wait=True)
         return stats
@@ -333,11 +366,16 @@ def main(argv=None):
     ap.add_argument("--group-max-ados", type=int, default=200000, help="largest request batched in ticks")
     ap.add_argument("--group-max-cost", type=float, default=4e6,
                     help="largest ADOs x n_states^2 of a request batched in ticks")
+    ap.add_argument("--autotune", type=int, default=-1,
+                    help="timed launches per schedule candidate when a run is created (0: no tuning, the "
+                         "cached or default schedules; -1: the library's setting)")
     ap.add_argument("--dump", default="", help="write every request's timeline to <dump>_<rate>.jsonl")
     ap.add_argument("--large-occupancy", type=int, default=800,
                     help="occupancy_pct of a larger request's stage launches (above 100: waves of CTAs)")
     args = ap.parse_args(argv)
     heom.load()
+    if args.autotune >= 0:
+        heom.set_autotune(args.autotune)
     cap = args.max_ado_steps if args.max_ado_steps > 0 else None
     for rate in args.rates:
         reqs = wl.serving_stream(rate, args.requests, max_ado_steps=cap)
@@ -353,7 +391,9 @@ def main(argv=None):
         s.update({"offered_rate_req_per_s": rate, "max_ado_steps": cap, "precision": args.precision,
                   "workers": args.workers, "max_active": args.max_active, "quantum": args.quantum,
                   "group_max_ados": args.group_max_ados, "group_max_cost": args.group_max_cost,
-                  "large_occupancy_pct": args.large_occupancy,
+                  "large_occupancy_pct": args.large_occupancy, "autotune": args.autotune,
+                  "loop_host_s": {k: {"total": round(v[0], 3), "longest": round(v[1], 3), "count": v[2]}
+                                  for k, v in st.loop.items()},
                   "rejected_fraction": s["rejected"] / max(s["requests"], 1)})
         print(json.dumps(s), flush=True)
     return 0
