@@ -450,7 +450,8 @@ def time_serving(rates=(5.0, 20.0, 50.0), n_requests=100, max_ado_steps=2e7, bud
             "server": f"up to {max_active} requests admitted; small requests (<= 200,000 ADOs and <= 4e6 ADOs x "
                       f"n_states^2) advance in batched ticks of one heom_group_propagate call (work-list launches "
                       f"per size class) on a high-priority stream, larger ones on their own streams with CUDA "
-                      f"graphs and grids of 8 CTA waves; quantum 100 steps",
+                      f"graphs and grids of 8 CTA waves; quantum 100 steps (at most 2e10 ADOs x n_states^2 x "
+                      f"steps for a larger request); no autotuning at set-up",
             "budget_bytes": budget, "full_mix_rejected_fraction": rej / len(full), "legs": legs}
 
 

@@ -77,6 +77,8 @@ class _Active:
     nbytes: int
     graph: object = None
     small: bool = False  # advanced in the batched ticks (heom_group_propagate)
+    quantum: int = 0      # steps per quantum of a larger request
+    graph_steps: int = 0  # steps per replay of its graph
 
 
 @dataclass
@@ -110,7 +112,7 @@ class Server:
     def __init__(self, budget_bytes: float = 120e9, precision: str = "fp32_mixed", quantum: int = 100,
                  max_active: int = 64, obs_stride: int = 0, keep_sigma0: bool = False, graph_steps: int | None = None,
                  workers: int = 4, group_max_ados: int = 200000, group_max_cost: float = 4e6,
-                 large_occupancy_pct: int = 800):
+                 large_occupancy_pct: int = 800, quantum_cost: float = 2e10, autotune: int = 0):
         if obs_stride > 0 and quantum % obs_stride:
             raise ValueError("obs_stride must divide quantum")
         if graph_steps is None:  # one graph per quantum (measured: fewer, longer graphs serve more)
@@ -136,6 +138,15 @@ class Server:
         # launch; below 100 a persistent grid on that share of each SM's CTA slots (measured on the full
         # mix: 50 % slowed the largest request more than it helped the rest)
         self.large_occupancy_pct = int(large_occupancy_pct)
+        # a larger request's quantum holds at most this many ADOs x n_states^2 x steps (0: no bound), so
+        # that no request's queued launches occupy the GPU for long: work queued on streams that share a
+        # hardware queue with it, and host calls that wait for such work, wait behind a whole quantum
+        # (measured on the full mix: 100 steps of the 7M-ADO request, about 9 s, stalled the loop)
+        self.quantum_cost = float(quantum_cost)
+        # timed launches per candidate schedule when a request's run is created (heom_set_autotune);
+        # 0: no tuning, cached or default schedules (measured on the full mix: tuning new runs while the
+        # GPU is busy held their set-up for seconds, p50 68 s against 16 s); -1: the library's setting
+        self.autotune = int(autotune)
         self._hier_cache = {}
 
     def _hier(self, heom, M, D):
@@ -143,6 +154,16 @@ class Server:
         if key not in self._hier_cache:
             self._hier_cache[key] = heom.Hierarchy(M, D)
         return self._hier_cache[key]
+
+    def _quantum(self, r) -> tuple[int, int]:
+        """Steps per quantum of a larger request and steps per replay of its graph."""
+        s = r.prop.system
+        q = self.quantum
+        if self.quantum_cost > 0:
+            q = min(q, int(self.quantum_cost // max(1, s.n_ado * s.N * s.N)))
+        unit = self.graph_steps if self.graph_steps < self.quantum else max(self.obs_stride, 1)
+        q = max(unit, q - q % unit)
+        return q, (self.graph_steps if self.graph_steps < self.quantum else q)
 
     def _small(self, r) -> bool:
         s = r.prop.system
@@ -163,8 +184,9 @@ class Server:
                 run.set_schedule(self.large_occupancy_pct, 1, part=0)
             t1 = time.perf_counter()
             graph = None
-            if r.prop.n_steps >= self.quantum and not self._small(r):
-                graph = heom.Batch([run], r.prop.dt_fs, self.graph_steps, self.obs_stride)
+            q, gsteps = self._quantum(r)
+            if r.prop.n_steps >= q and not self._small(r):
+                graph = heom.Batch([run], r.prop.dt_fs, gsteps, self.obs_stride)
         return run, graph, t1 - t0, time.perf_counter() - t1
 
     def serve(self, requests, real_time: bool = True) -> ServeStats:
@@ -175,6 +197,7 @@ class Server:
         from . import heom
 
         heom.load()
+        prev_tune = heom.set_autotune(self.autotune) if self.autotune >= 0 else None
         reqs = sorted(requests, key=lambda r: r.arrival_s)
         arrivals = deque(reqs)
         pending: deque = deque()
@@ -213,7 +236,9 @@ class Server:
             res.batched = self._small(r)
             ev = torch.cuda.Event()
             ev.record(streams[si])
-            active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph, self._small(r)))
+            q, gsteps = self._quantum(r)
+            active.append(_Active(r, run, si, ev, r.prop.n_steps, res, res.workspace_bytes, graph, self._small(r),
+                                  q, gsteps))
 
         def complete(a):
             nonlocal used
@@ -318,9 +343,9 @@ class Server:
                 if a.remaining > 0:
                     st = streams[a.stream]
                     with timed("quantum launch (larger requests)"):
-                        if a.graph is not None and a.remaining >= self.quantum:
-                            a.graph.launch(self.quantum // self.graph_steps)
-                            q = self.quantum
+                        if a.graph is not None and a.remaining >= a.quantum:
+                            a.graph.launch(a.quantum // a.graph_steps)
+                            q = a.quantum
                         else:
                             q = a.remaining
                             a.run.propagate(a.req.prop.dt_fs, q, self.obs_stride)
@@ -338,6 +363,8 @@ class Server:
         stats = ServeStats(results=[results[k] for k in sorted(results)], wall_s=now(), loop=loop)
         if pool is not None:
             pool.shutdown(wait=True)
+        if prev_tune is not None:
+            heom.set_autotune(prev_tune)
         return stats
 
 
@@ -366,23 +393,24 @@ def main(argv=None):
     ap.add_argument("--group-max-ados", type=int, default=200000, help="largest request batched in ticks")
     ap.add_argument("--group-max-cost", type=float, default=4e6,
                     help="largest ADOs x n_states^2 of a request batched in ticks")
-    ap.add_argument("--autotune", type=int, default=-1,
+    ap.add_argument("--autotune", type=int, default=0,
                     help="timed launches per schedule candidate when a run is created (0: no tuning, the "
                          "cached or default schedules; -1: the library's setting)")
+    ap.add_argument("--quantum-cost", type=float, default=2e10,
+                    help="bound on ADOs x n_states^2 x steps of a larger request's quantum (0: none)")
     ap.add_argument("--dump", default="", help="write every request's timeline to <dump>_<rate>.jsonl")
     ap.add_argument("--large-occupancy", type=int, default=800,
                     help="occupancy_pct of a larger request's stage launches (above 100: waves of CTAs)")
     args = ap.parse_args(argv)
     heom.load()
-    if args.autotune >= 0:
-        heom.set_autotune(args.autotune)
     cap = args.max_ado_steps if args.max_ado_steps > 0 else None
     for rate in args.rates:
         reqs = wl.serving_stream(rate, args.requests, max_ado_steps=cap)
         st = Server(budget_bytes=args.budget, precision=args.precision, quantum=args.quantum,
                     workers=args.workers, max_active=args.max_active, group_max_ados=args.group_max_ados,
                     group_max_cost=args.group_max_cost,
-                    large_occupancy_pct=args.large_occupancy).serve(reqs, real_time=True)
+                    large_occupancy_pct=args.large_occupancy, quantum_cost=args.quantum_cost,
+                    autotune=args.autotune).serve(reqs, real_time=True)
         s = st.summary()
         if args.dump:
             with open(f"{args.dump}_{rate:g}.jsonl", "w") as fh:
@@ -392,6 +420,7 @@ def main(argv=None):
                   "workers": args.workers, "max_active": args.max_active, "quantum": args.quantum,
                   "group_max_ados": args.group_max_ados, "group_max_cost": args.group_max_cost,
                   "large_occupancy_pct": args.large_occupancy, "autotune": args.autotune,
+                  "quantum_cost": args.quantum_cost,
                   "loop_host_s": {k: {"total": round(v[0], 3), "longest": round(v[1], 3), "count": v[2]}
                                   for k, v in st.loop.items()},
                   "rejected_fraction": s["rejected"] / max(s["requests"], 1)})

@@ -73,6 +73,14 @@ def fake_modules(state, sizes):
 
     heom.Run = Run
     heom.Batch = Batch
+    state.autotune = [3]
+
+    def set_autotune(reps):
+        prev = state.autotune[-1]
+        state.autotune.append(reps)
+        return prev
+
+    heom.set_autotune = set_autotune
 
     def group_propagate(runs, dt, steps, obs_stride=0, stream=None):
         state.ticks.append({r.name: q for r, q in zip(runs, steps)})
@@ -185,3 +193,26 @@ def test_small_requests_advance_in_batched_ticks(monkeypatch, workers):
     assert all(q <= 100 for t in state.ticks for q in t.values())
     assert max(len(t) for t in state.ticks) >= 2
     assert state.used == 0
+
+
+def test_cost_bounded_quantum_and_autotune(monkeypatch):
+    """A larger request whose quantum would hold more than quantum_cost ADOs x n_states^2 x steps takes
+    shorter quanta (here 6 ADOs x 2^2 x 30 steps = 720: 30-step graphs); run creation happens with the
+    autotuner off, and the library's setting is restored afterwards."""
+    import torch
+
+    import paper_1803_03498_gb300 as pkg
+
+    state = FakeState()
+    sizes = {"a": 10, "b": 10}
+    heom, cuda = fake_modules(state, sizes)
+    monkeypatch.setattr(pkg, "heom", heom, raising=False)
+    monkeypatch.setitem(__import__("sys").modules, "paper_1803_03498_gb300.heom", heom)
+    monkeypatch.setattr(torch, "cuda", cuda)
+    reqs = make_requests([("a", 250), ("b", 20)])
+    assert reqs[0].prop.system.n_ado == 6
+    srv = serving.Server(budget_bytes=100, quantum=100, max_active=4, workers=0, group_max_ados=0, quantum_cost=720)
+    stats = srv.serve(reqs, real_time=False)
+    assert all(not r.rejected and np.isfinite(r.done_s) for r in stats.results)
+    assert state.graph_launches == {"a": 240} and state.tails == {"a": 10, "b": 20}
+    assert state.autotune == [3, 0, 3]
