@@ -64,7 +64,7 @@ def _traffic():
 
     src = os.path.join(ROOT, "paper_1803_03498_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("stage_kernel.cuh", "stage_col.cuh", "propagate.cu"):  # the kernels and the driver that launches them
+    for f in ("stage_kernel.cuh", "stage_col.cuh", "propagate.cu"):  # the kernels and the host code that launches them
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
     vals = {}
